@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Throughput of the tridiagonal partition solve on GB300.
+
+Workload: one strictly diagonally dominant tridiagonal system of
+n = 2^27 unknowns (a, c ~ U(-1,1), b = |a| + |c| + U(1,2), x_true ~ U(-1,1),
+d = A x_true; fp64 I/O, 5.4 GB for a, b, c, d, x), the large single-system
+case of the method.  One step = one full solve (Stage 1, the recursive
+Stage 2, Stage 3).
+
+  value    solved unknowns/s, device-resident inputs, tuned path
+           (double-float arithmetic on the fp32 pipes, fp64 I/O)
+  plain    the same with native fp64 arithmetic (the plain partition solve)
+  e2e      tps_solve_host_async from pinned host buffers: chunked H2D,
+           kernels and D2H on the plan's streams, all inside the timed region
+  roofline the dominant kernel's algorithmic bytes over its mean duration
+           (CUDA events recorded by the library on the launch stream during
+           the timed steps) against the measured HBM copy bandwidth
+  cpu_baseline  the serial fp64 Thomas oracle on the host cores (rank 0,
+           one GPU only); its solution also gives the GPU result's error
+
+Multi-GPU: every rank solves its own independent system (replicas, weak
+scaling, no collective on the data path); value is the sum over ranks.
+
+``--impl reference`` times the CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solved unknowns/s (partition method, n=2^27, err<=1e-10 vs fp64 oracle)"
+UNIT = "unknowns/s"
+N_DEFAULT = 1 << 27
+SEED = 1002
+
+
+def args_():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="tps", choices=["tps", "reference"])
+    p.add_argument("--n", type=int, default=N_DEFAULT)
+    p.add_argument("--m", type=int, default=0)
+    p.add_argument("--m-reduced", type=int, default=0)
+    p.add_argument("--streams", type=int, default=0)
+    p.add_argument("--chunk", type=int, default=0)
+    p.add_argument("--e2e-steps", type=int, default=0)
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_table():
+    """Per-row DRAM bytes of each kernel from the committed ncu summary."""
+    out = {}
+    path = os.path.join(ROOT, "profiles", "dram_traffic_per_row.txt")
+    if os.path.exists(path):
+        with open(path) as f:
+            for line in f:
+                if line.startswith("#") or not line.strip():
+                    continue
+                k, v = line.split()[:2]
+                out[k] = float(v)
+    return out
+
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed regions run."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in getattr(self, "lines", []):
+            f = [v.strip() for v in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init(gpus):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_device(plan, g, x, steps, warmup, world, stream):
+    import torch
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            plan.solve(g["a"], g["b"], g["c"], g["d"], x, stream=stream)
+        plan.query()  # clears the trace ring and the status word
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            plan.solve(g["a"], g["b"], g["c"], g["d"], x, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    info = plan.query()
+    return max_over_ranks(ms, world), info
+
+
+def verify(g, x):
+    """Error against the manufactured solution and the fp64 residual, on the
+    device with plain PyTorch ops (verification only)."""
+    import torch
+
+    a, b, c, d, xt = g["a"], g["b"], g["c"], g["d"], g["x_true"]
+    ex = (x - xt).abs().max().item() / xt.abs().max().item()
+    r = d - b * x
+    r[1:] -= a[1:] * x[:-1]
+    r[:-1] -= c[:-1] * x[1:]
+    rr = r.abs().max().item() / d.abs().max().item()
+    return ex, rr
+
+
+def cpu_oracle_leg(g, x_gpu, budget_s=12.0):
+    """The serial Thomas oracle on the full system; returns the throughput
+    and the GPU result's relative forward error against it."""
+    import numpy as np
+
+    import oracle
+
+    a, b, c, d = (g[k].cpu().numpy() for k in "abcd")
+    n = b.shape[0]
+    oracle.build()
+    times, ref = [], None
+    t_end = time.perf_counter() + budget_s
+    while True:
+        t0 = time.perf_counter()
+        ref = oracle.thomas(a, b, c, d)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() + times[-1] > t_end or len(times) >= 20:
+            break
+    xg = x_gpu.cpu().numpy()
+    err = oracle.rel_forward_error(xg, ref)
+    res = oracle.rel_residual(a, b, c, d, xg)
+    best = min(times)
+    return {"value": n / best, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"serial fp64 Thomas oracle on the full n={n} system, best of "
+                      f"{len(times)} solves ({sum(times):.1f} s of CPU work)"}, err, res, ref
+
+
+def reference_arm(a):
+    """The CPU oracle as the reference arm: rank 0 only."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2501_05938_gb300 import synth
+
+    n = min(a.n, 1 << 23)
+    s = synth.system(SEED, n)
+    oracle.build()
+    for _ in range(a.warmup):
+        oracle.thomas(s["a"], s["b"], s["c"], s["d"])
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        oracle.thomas(s["a"], s["b"], s["c"], s["d"])
+    dt = (time.perf_counter() - t0) / a.steps
+    v = n / dt
+    sample = (f"serial fp64 Thomas oracle, one step = one solve of an n={n} prefix-size system "
+              f"from the same generator")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "single SDD tridiagonal system (fp64 oracle on host cores)",
+                       "n": n, "world_size": world},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = args_()
+    if a.impl == "reference":
+        reference_arm(a)
+        return
+    import torch
+
+    from paper_2501_05938_gb300 import binding, synth
+
+    world, rank, local = dist_init(a.gpus)
+    dev = torch.cuda.current_device()
+    n = a.n
+    seed = SEED + rank
+    stream = torch.cuda.Stream()
+    g = synth.system_device(seed, n)
+    x = torch.empty_like(g["b"])
+    torch.cuda.synchronize()
+    hbm_peak, peak_kind = peaks()
+    out = {}
+    with Clocks(dev) as clk:
+        # tuned: double-float arithmetic
+        plan = binding.Plan(n, dtype="f64_df", m=a.m, m_reduced=a.m_reduced,
+                            flags=binding.TRACE)
+        ms, info = time_device(plan, g, x, a.steps, a.warmup, world, stream)
+        err_true, res = verify(g, x)
+        # plain: native fp64 arithmetic
+        xp = torch.empty_like(x)
+        plan_p = binding.Plan(n, dtype="f64", m=a.m, m_reduced=a.m_reduced, flags=binding.TRACE)
+        msp, infop = time_device(plan_p, g, xp, max(3, a.steps // 4), min(a.warmup, 3), world,
+                                 stream)
+        err_true_p, res_p = verify(g, xp)
+        del xp
+        # end to end from pinned host buffers
+        hk = {k: g[k].cpu().pin_memory() for k in "abcd"}
+        hx = torch.empty(n, dtype=torch.float64).pin_memory()
+        plan_h = binding.Plan(n, dtype="f64_df", residency="host", m=a.m, m_reduced=a.m_reduced,
+                              streams=a.streams, chunk=a.chunk)
+        esteps = a.e2e_steps or max(3, min(a.steps, 20))
+        for _ in range(min(a.warmup, 3)):
+            plan_h.solve_host_async(hk["a"], hk["b"], hk["c"], hk["d"], hx, stream=stream)
+        stream.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(esteps):
+            plan_h.solve_host_async(hk["a"], hk["b"], hk["c"], hk["d"], hx, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        barrier(world)
+        ems = max_over_ranks(e0.elapsed_time(e1) / esteps, world)
+        infoh = plan_h.query()
+        eh_err = (hx.to("cuda") - g["x_true"]).abs().max().item() / g["x_true"].abs().max().item()
+    clocks = clk.summary()
+
+    value = world * n / (ms * 1e-3)
+    s1, s2, s3, tot = info["stage_ms"]
+    dominant = "k_stage1" if s1 >= s3 else "k_stage3"
+    dom_ms = max(s1, s3)
+    alg_bytes = (32 if dominant == "k_stage1" else 40) * n
+    achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
+    traffic = traffic_table().get(f"{dominant}_f64_df")
+    levels = info["levels"]
+    launches_per_step = 2 * levels + 1
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32x2", "data": "synthetic",
+        "config": {"workload": "single SDD tridiagonal system, n=2^27, fp64 I/O, device-resident",
+                   "n": n, "m": info["m"], "m_reduced": info["m_reduced"], "levels": levels,
+                   "io": "f64", "arith": "double-float (fp32 pairs, ~2^-46/op)",
+                   "l2": "inputs (5.4 GB) larger than L2, no flush",
+                   "parallelism": f"replicas x{world}"},
+        "gpu_launches": launches_per_step * a.steps,
+        "err": {"rel_fwd_vs_x_true": err_true, "rel_residual": res},
+        "stage_ms": {"stage1": s1, "stage2": s2, "stage3": s3, "total": tot},
+        "plain": {"value": world * n / (msp * 1e-3), "ms_per_step": msp, "dtype": "f64",
+                  "stage_ms": infop["stage_ms"],
+                  "err": {"rel_fwd_vs_x_true": err_true_p, "rel_residual": res_p}},
+        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": achieved / hbm_peak,
+                     "traffic": (traffic * n if traffic else None),
+                     "peak_kind": peak_kind,
+                     "alg_bytes_per_row": alg_bytes // n},
+        "e2e": {"value": world * n / (ems * 1e-3), "unit": UNIT, "ms_per_step": ems,
+                "steps": esteps, "h2d_bytes_per_step": 4 * 8 * n, "d2h_bytes_per_step": 8 * n,
+                "streams": infoh["streams"], "chunk": infoh["chunk"],
+                "rel_fwd_vs_x_true": eh_err},
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not a.no_cpu:
+        cpu, err_o, res_o, _ = cpu_oracle_leg(g, x)
+        line["cpu_baseline"] = cpu
+        line["err"]["rel_fwd_vs_oracle"] = err_o
+        line["err"]["rel_residual_host"] = res_o
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

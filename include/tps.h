@@ -1,0 +1,169 @@
+/*
+ * tps.h -- C ABI of libtps, a GB300 (sm_103a) solver for tridiagonal systems
+ * by the partition method.
+ *
+ * The method (paper Sec. 1, citing Austin et al. 2004; Sec. 2.2) splits the
+ * n x n tridiagonal matrix into blocks of m consecutive rows and solves
+ *   Stage 1  per block: eliminate the interior rows, leaving two equations
+ *            in the block's first and last unknown (its interface unknowns);
+ *   Stage 2  the reduced tridiagonal system in all interface unknowns;
+ *   Stage 3  per block: recover the interior unknowns from the interface
+ *            values.
+ * Here all three stages run on the GPU; Stage 2 applies the same method
+ * recursively and finishes with parallel cyclic reduction in one warp.  The
+ * host-resident pipeline (Sec. 2.2, Eq. 2) overlaps chunked host-to-device
+ * copies, kernels and device-to-host copies on S CUDA streams, S a power of
+ * two up to 32 (Sec. 2.1).
+ *
+ * Conventions shared by every entry point
+ *   Row i reads  a[i]*x[i-1] + b[i]*x[i] + c[i]*x[i+1] = d[i].  a[0] and
+ *   c[n-1] (per system in a batch) are never used, so packed systems never
+ *   couple.  Arrays are contiguous, one element per row, of the plan's I/O
+ *   type (double for TPS_F64, TPS_F64_DF and TPS_MIXED_F32_F64; float for
+ *   TPS_F32).  The caller owns every array; inputs are not modified; x must
+ *   not overlap an input.  The matrix should be strictly diagonally
+ *   dominant (no pivoting is done); a zero or non-finite pivot is reported
+ *   through tps_plan_query, not by the return value.
+ *   Calls are stream-ordered and asynchronous: argument and launch errors
+ *   come back as the return value, numeric errors (TPS_ERR_ZERO_PIVOT,
+ *   TPS_ERR_NO_CONVERGENCE) from tps_plan_query after the stream has been
+ *   synchronised.  A plan may be used by one stream at a time.
+ *   `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ */
+#ifndef TPS_H
+#define TPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TPS_OK = 0,
+  TPS_ERR_INVALID_ARG = 1,    /* bad pointer, size, alias, or plan misuse      */
+  TPS_ERR_UNSUPPORTED = 2,    /* valid request this build does not serve       */
+  TPS_ERR_CUDA = 3,           /* a CUDA runtime call failed                    */
+  TPS_ERR_OOM = 4,            /* device or pinned allocation failed            */
+  TPS_ERR_ZERO_PIVOT = 5,     /* zero/non-finite pivot met (matrix not SDD)    */
+  TPS_ERR_NO_CONVERGENCE = 6, /* mixed-precision refinement did not converge   */
+  TPS_ERR_TIMEOUT = 7         /* a bounded device-side wait gave up            */
+} tps_status;
+
+typedef enum {
+  TPS_F64 = 0,           /* fp64 I/O, native fp64 arithmetic (the plain solve)  */
+  TPS_F32 = 1,           /* fp32 I/O and arithmetic                             */
+  TPS_MIXED_F32_F64 = 2, /* fp64 I/O; fp32 elimination, fp64 residual/update,   */
+                         /* iterative refinement to the plan's tolerance        */
+  TPS_F64_DF = 3         /* fp64 I/O; double-float arithmetic (pairs of fp32)   */
+                         /* on the fp32 pipes, about 2^-46 relative per op;     */
+                         /* for magnitudes in [2^-103, 2^127]                   */
+} tps_dtype;
+
+typedef enum {
+  TPS_DEVICE = 0,     /* arrays in device memory (tps_solve, tps_solve_batched) */
+  TPS_HOST_PINNED = 1 /* arrays in pinned host memory (tps_solve_host_async)    */
+} tps_residency;
+
+/* tps_plan_desc.flags */
+#define TPS_TUNE_PREDICT 1u       /* fill zero m/streams/chunk from the predictor */
+#define TPS_TUNE_EXHAUSTIVE 2u    /* time the candidate grid on the device        */
+#define TPS_TRACE 4u              /* record per-stage event times (tps_plan_query) */
+#define TPS_EXTERNAL_WORKSPACE 8u /* caller supplies the workspace                */
+
+typedef struct {
+  int64_t n_max;     /* largest n of tps_solve / tps_solve_host_async, or the  */
+                     /* largest total row count of tps_solve_batched           */
+  int64_t batch_max; /* largest system count of tps_solve_batched (0: none)    */
+  int32_t dtype;     /* tps_dtype                                              */
+  int32_t residency; /* tps_residency (informs the predictor)                  */
+  int32_t m;         /* rows per block at the top level; 0 = choose            */
+  int32_t m_reduced; /* rows per block at the recursive levels; 0 = choose     */
+  int32_t streams;   /* S for tps_solve_host_async (1..32); 0 = choose         */
+  int32_t max_iters; /* refinement iteration cap; 0 = 10                       */
+  int64_t chunk;     /* rows per host-pipeline chunk; 0 = choose               */
+  double tol;        /* refinement stop: ||delta||/||x|| <= tol; 0 = 1e-12     */
+  uint32_t flags;    /* TPS_TUNE_* | TPS_TRACE | TPS_EXTERNAL_WORKSPACE        */
+  uint32_t reserved; /* must be 0                                              */
+} tps_plan_desc;
+
+typedef struct tps_plan_s* tps_plan_t;
+
+typedef struct {
+  int32_t status;        /* tps_status of the numeric checks since the last query */
+  int32_t iterations;    /* refinement iterations of the last mixed solve         */
+  int32_t m;             /* parameters the plan uses                              */
+  int32_t m_reduced;
+  int32_t streams;
+  int32_t levels;        /* partition levels of the last solve                    */
+  int64_t chunk;
+  double last_correction; /* ||delta||/||x|| of the last refinement step          */
+  float stage_ms[4];     /* TPS_TRACE: stage 1, stage 2, stage 3, total (last solve) */
+  size_t workspace_bytes;
+} tps_info;
+
+/* Create a plan.  Validates `desc` (n_max >= 0, dtype, m 0 or >= 2, streams
+ * 0 or 1..32, reserved == 0), resolves zero parameters (predictor when
+ * TPS_TUNE_PREDICT is set, fixed defaults otherwise), creates the streams
+ * and events of the host pipeline and, unless TPS_EXTERNAL_WORKSPACE is set,
+ * allocates the device workspace.  On failure *out is NULL. */
+tps_status tps_plan(const tps_plan_desc* desc, tps_plan_t* out);
+
+/* Release everything the plan owns (not a caller-supplied workspace).  The
+ * caller must make sure no solve on the plan is still running. */
+tps_status tps_plan_destroy(tps_plan_t plan);
+
+/* Device workspace the plan needs for n_max / batch_max, in bytes. */
+tps_status tps_workspace_size(tps_plan_t plan, size_t* bytes);
+
+/* Hand the plan a caller-owned device buffer of at least
+ * tps_workspace_size bytes (256-byte aligned).  Only for plans created with
+ * TPS_EXTERNAL_WORKSPACE; the buffer must outlive every solve. */
+tps_status tps_set_workspace(tps_plan_t plan, void* dev_ptr, size_t bytes);
+
+/* Solve one system of n <= n_max rows held in device memory (Sec. 2.2,
+ * Stages 1-3 on the GPU).  a, b, c, d, x: device pointers to n elements of
+ * the plan's I/O type, 8-byte aligned for fp64, 4-byte for fp32.  Enqueues
+ * the kernels on `stream` and returns; no host synchronisation, so it may
+ * be captured into a CUDA graph. */
+tps_status tps_solve(tps_plan_t plan, int64_t n, const void* a, const void* b, const void* c,
+                     const void* d, void* x, void* stream);
+
+/* Solve `count` independent systems packed back to back: system s owns rows
+ * offsets[s] .. offsets[s+1]-1.  offsets: device pointer to count+1 int64
+ * values, offsets[0] = 0, non-decreasing, offsets[count] <= n_max;
+ * host_offsets: the same values in host memory (used to build the work
+ * list; may be NULL, then the offsets are read back with a synchronous
+ * copy).  count <= batch_max. */
+tps_status tps_solve_batched(tps_plan_t plan, int64_t count, const int64_t* offsets,
+                             const int64_t* host_offsets, const void* a, const void* b,
+                             const void* c, const void* d, void* x, void* stream);
+
+/* Solve one system held in pinned host memory (cudaHostAlloc /
+ * cudaHostRegister): copies the rows to the device in chunks on the plan's
+ * S streams, overlapping each chunk's host-to-device copy with the Stage-1
+ * kernel of the previous chunk; then Stage 2; then per chunk Stage 3 and the
+ * device-to-host copy of x (Sec. 2.2, Eq. 2).  The device keeps its copy of
+ * a, b, c, d between the stages, so nothing is uploaded twice.  Work is
+ * ordered after everything already in `stream`, and `stream` waits for all
+ * of it; the call returns after enqueueing.  Pageable memory gives
+ * TPS_ERR_INVALID_ARG. */
+tps_status tps_solve_host_async(tps_plan_t plan, int64_t n, const void* a, const void* b,
+                                const void* c, const void* d, void* x, void* stream);
+
+/* Report the plan's parameters and the numeric status of the solves since
+ * the previous query (synchronises the plan's last stream, reads the device
+ * status word and clears it). */
+tps_status tps_plan_query(tps_plan_t plan, tps_info* out);
+
+/* Static description of a status code. */
+const char* tps_status_string(tps_status s);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int tps_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPS_H */

@@ -1,0 +1,234 @@
+// Recursive device-resident partition solve: Stage 1 on the input, the same
+// method on the reduced interface system (Stage 2) until it fits one warp,
+// then Stage 3 back up the levels.
+#include <cuda_runtime.h>
+
+#include <type_traits>
+#include <vector>
+
+#include "tps_internal.h"
+
+namespace tps {
+
+Level make_level(int64_t n, int m, int R) {
+  Level lv{};
+  lv.n = n;
+  lv.m = m;
+  int64_t p = (n + m - 1) / m;
+  int64_t last = n - (p - 1) * (int64_t)m;
+  if (last == 1 && p > 1) {  // merge a one-row tail into the previous block
+    p -= 1;
+    last = m + 1;
+  }
+  lv.p = p;
+  lv.k_begin = 0;
+  lv.k_end = p;
+  lv.llast = (int32_t)last;
+  // checkpoint slots: a block of length L has floor((L - 2) / R) of them;
+  // size for the longest block (m + 1) so the count is monotone in n
+  lv.ncap = (m + 1 - 2) >= R ? (m + 1 - 2) / R : 0;
+  return lv;
+}
+
+size_t build_levels(int64_t n, int m0, int mr, size_t top_elem, size_t red_elem, size_t base,
+                    std::vector<LevelPlan>& out) {
+  out.clear();
+  size_t off = base;
+  int64_t N = n;
+  size_t elem = top_elem;
+  int m = m0;
+  while (N > kBaseMax) {
+    LevelPlan L{};
+    L.R = chunk_rows(elem);
+    L.lv = make_level(N, m, L.R);
+    const int64_t nr = 2 * L.lv.p;
+    for (int i = 0; i < 5; ++i) {
+      L.off_red[i] = off;
+      off = align_up(off + (size_t)nr * red_elem);
+    }
+    const size_t nck = (size_t)L.lv.ncap * (size_t)L.lv.p;
+    for (int i = 0; i < 3; ++i) {
+      L.off_ck[i] = off;
+      off = align_up(off + nck * red_elem);
+    }
+    out.push_back(L);
+    N = nr;
+    elem = red_elem;
+    m = mr;
+  }
+  return off;
+}
+
+size_t elem_bytes_io(int dtype) { return dtype == TPS_F32 ? 4 : 8; }
+size_t elem_bytes_red(int dtype) { return dtype == TPS_F32 ? 4 : 8; }
+
+// ------------------------------------------------------------------ launchers
+template <class Ar, class Tin, class Tred, int R>
+static cudaError_t launch_stage1(const Level& lv, const Tin* a, const Tin* b, const Tin* c,
+                                 const Tin* d, Tred* ra, Tred* rb, Tred* rc, Tred* rd, Tred* cg,
+                                 Tred* cy, Tred* cv, int* status, cudaStream_t s) {
+  constexpr int W = kWarpsPerCta;
+  const size_t smem = WarpTile<Tin, R>::kBytesPerWarp * W;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_stage1<Ar, Tin, Tred, R, W>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int64_t warps = (lv.k_end - lv.k_begin + 31) / 32;
+  const unsigned grid = (unsigned)((warps + W - 1) / W);
+  if (grid == 0) return cudaSuccess;
+  k_stage1<Ar, Tin, Tred, R, W><<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, ra, rb, rc, rd, cg, cy,
+                                                           cv, status);
+  return cudaGetLastError();
+}
+
+template <class Ar, class Tin, class Tred, int R>
+static cudaError_t launch_stage3(const Level& lv, const Tin* a, const Tin* b, const Tin* c,
+                                 const Tin* d, const Tred* xr, const Tred* cg, const Tred* cy,
+                                 const Tred* cv, Tin* x, int* status, cudaStream_t s) {
+  constexpr int W = kWarpsPerCta;
+  const size_t smem = WarpTile<Tin, R>::kBytesPerWarp * W;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_stage3<Ar, Tin, Tred, R, W>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int64_t warps = (lv.k_end - lv.k_begin + 31) / 32;
+  const unsigned grid = (unsigned)((warps + W - 1) / W);
+  if (grid == 0) return cudaSuccess;
+  k_stage3<Ar, Tin, Tred, R, W><<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, xr, cg, cy, cv, x,
+                                                           status);
+  return cudaGetLastError();
+}
+
+template <class Ar, class Tin, class Tred>
+static cudaError_t run_levels(tps_plan_s* P, const std::vector<LevelPlan>& levels, size_t idx,
+                              int64_t n, const Tin* a, const Tin* b, const Tin* c, const Tin* d,
+                              Tin* x, cudaStream_t s) {
+  if (idx == levels.size()) {
+    if (n <= 0) return cudaSuccess;
+    k_base<Ar, Tin, Tin><<<1, 32, 0, s>>>(n, a, b, c, d, x, P->d_status);
+    return cudaGetLastError();
+  }
+  const LevelPlan& L = levels[idx];
+  constexpr int R = sizeof(Tin) >= 8 ? 8 : 16;
+  Tred* red[5];
+  for (int i = 0; i < 5; ++i) red[i] = reinterpret_cast<Tred*>(P->ws + L.off_red[i]);
+  Tred* ck[3];
+  for (int i = 0; i < 3; ++i) ck[i] = reinterpret_cast<Tred*>(P->ws + L.off_ck[i]);
+  cudaError_t e = launch_stage1<Ar, Tin, Tred, R>(L.lv, a, b, c, d, red[0], red[1], red[2], red[3],
+                                                  ck[0], ck[1], ck[2], P->d_status, s);
+  if (e != cudaSuccess) return e;
+  e = run_levels<Ar, Tred, Tred>(P, levels, idx + 1, 2 * L.lv.p, red[0], red[1], red[2], red[3],
+                                 red[4], s);
+  if (e != cudaSuccess) return e;
+  return launch_stage3<Ar, Tin, Tred, R>(L.lv, a, b, c, d, red[4], ck[0], ck[1], ck[2], x,
+                                         P->d_status, s);
+}
+
+// ------------------------------------------------------------------ dtype dispatch
+// Level-0 pieces, used by the device path (with optional stage events) and
+// by the chunked host pipeline.
+template <class F>
+static cudaError_t dispatch(int dtype, F&& f) {
+  switch (dtype) {
+    case TPS_F64: return f(ArF64{}, (double*)nullptr, (double*)nullptr);
+    case TPS_F64_DF: return f(ArDF{}, (double*)nullptr, (float2*)nullptr);
+    case TPS_F32: return f(ArF32{}, (float*)nullptr, (float*)nullptr);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t stage1_range(tps_plan_s* P, const LevelPlan& L, int64_t kb, int64_t ke,
+                         const void* a, const void* b, const void* c, const void* d,
+                         cudaStream_t s) {
+  return dispatch(P->desc.dtype, [&](auto ar, auto* tin, auto* tred) -> cudaError_t {
+    using Ar = decltype(ar);
+    using Tin = std::remove_pointer_t<decltype(tin)>;
+    using Tred = std::remove_pointer_t<decltype(tred)>;
+    constexpr int R = sizeof(Tin) >= 8 ? 8 : 16;
+    Level lv = L.lv;
+    lv.k_begin = kb;
+    lv.k_end = ke;
+    Tred* red[4];
+    for (int i = 0; i < 4; ++i) red[i] = reinterpret_cast<Tred*>(P->ws + L.off_red[i]);
+    Tred* ck[3];
+    for (int i = 0; i < 3; ++i) ck[i] = reinterpret_cast<Tred*>(P->ws + L.off_ck[i]);
+    return launch_stage1<Ar, Tin, Tred, R>(lv, (const Tin*)a, (const Tin*)b, (const Tin*)c,
+                                           (const Tin*)d, red[0], red[1], red[2], red[3], ck[0],
+                                           ck[1], ck[2], P->d_status, s);
+  });
+}
+
+cudaError_t stage3_range(tps_plan_s* P, const LevelPlan& L, int64_t kb, int64_t ke,
+                         const void* a, const void* b, const void* c, const void* d, void* x,
+                         cudaStream_t s) {
+  return dispatch(P->desc.dtype, [&](auto ar, auto* tin, auto* tred) -> cudaError_t {
+    using Ar = decltype(ar);
+    using Tin = std::remove_pointer_t<decltype(tin)>;
+    using Tred = std::remove_pointer_t<decltype(tred)>;
+    constexpr int R = sizeof(Tin) >= 8 ? 8 : 16;
+    Level lv = L.lv;
+    lv.k_begin = kb;
+    lv.k_end = ke;
+    const Tred* xr = reinterpret_cast<const Tred*>(P->ws + L.off_red[4]);
+    const Tred* ck[3];
+    for (int i = 0; i < 3; ++i) ck[i] = reinterpret_cast<const Tred*>(P->ws + L.off_ck[i]);
+    return launch_stage3<Ar, Tin, Tred, R>(lv, (const Tin*)a, (const Tin*)b, (const Tin*)c,
+                                           (const Tin*)d, xr, ck[0], ck[1], ck[2], (Tin*)x,
+                                           P->d_status, s);
+  });
+}
+
+// Stage 2: the recursive solve of level 0's reduced system.
+cudaError_t reduced_solve(tps_plan_s* P, const std::vector<LevelPlan>& levels, cudaStream_t s) {
+  return dispatch(P->desc.dtype, [&](auto ar, auto* tin, auto* tred) -> cudaError_t {
+    using Ar = decltype(ar);
+    using Tred = std::remove_pointer_t<decltype(tred)>;
+    (void)tin;
+    const LevelPlan& L = levels[0];
+    Tred* red[5];
+    for (int i = 0; i < 5; ++i) red[i] = reinterpret_cast<Tred*>(P->ws + L.off_red[i]);
+    return run_levels<Ar, Tred, Tred>(P, levels, 1, 2 * L.lv.p, red[0], red[1], red[2], red[3],
+                                      red[4], s);
+  });
+}
+
+// The one-warp solve of a system of at most kBaseMax rows.
+cudaError_t base_solve(tps_plan_s* P, int64_t n, const void* a, const void* b, const void* c,
+                       const void* d, void* x, cudaStream_t s) {
+  return dispatch(P->desc.dtype, [&](auto ar, auto* tin, auto* tred) -> cudaError_t {
+    using Ar = decltype(ar);
+    using Tin = std::remove_pointer_t<decltype(tin)>;
+    (void)tred;
+    k_base<Ar, Tin, Tin><<<1, 32, 0, s>>>(n, (const Tin*)a, (const Tin*)b, (const Tin*)c,
+                                          (const Tin*)d, (Tin*)x, P->d_status);
+    return cudaGetLastError();
+  });
+}
+
+tps_status run_solve(tps_plan_s* P, int64_t n, const void* a, const void* b, const void* c,
+                     const void* d, void* x, cudaStream_t s, const std::vector<LevelPlan>& lv,
+                     cudaEvent_t* ev) {
+  cudaError_t e = cudaSuccess;
+  if (ev) e = cudaEventRecord(ev[0], s);
+  if (lv.empty()) {
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
+    if (e == cudaSuccess) e = base_solve(P, n, a, b, c, d, x, s);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
+  } else {
+    if (e == cudaSuccess) e = stage1_range(P, lv[0], 0, lv[0].lv.p, a, b, c, d, s);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
+    if (e == cudaSuccess) e = reduced_solve(P, lv, s);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
+    if (e == cudaSuccess) e = stage3_range(P, lv[0], 0, lv[0].lv.p, a, b, c, d, x, s);
+  }
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
+  return e == cudaSuccess ? TPS_OK : TPS_ERR_CUDA;
+}
+
+}  // namespace tps

@@ -1,0 +1,443 @@
+// C ABI of libtps: plans, workspace, the device-resident solve and the
+// host-resident streamed pipeline.  Declarations and contracts: include/tps.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "tps_internal.h"
+
+namespace tps {
+
+// Streams and events of the host-resident pipeline (Sec. 2.1-2.2: S streams,
+// S a power of two up to the 32 hardware queues).
+struct HostPipe {
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> ev_done1;   // per stream: its Stage-1 work is queued
+  std::vector<cudaEvent_t> ev_done3;   // per stream: its Stage-3 work is queued
+  cudaEvent_t ev_start = nullptr;      // caller's stream reached the solve
+  cudaEvent_t ev_red = nullptr;        // Stage 2 done
+  size_t off_dev = 0;                  // device working copies a, b, c, d, x
+};
+
+static tps_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return TPS_OK;
+  if (e == cudaErrorMemoryAllocation) return TPS_ERR_OOM;
+  return TPS_ERR_CUDA;
+}
+
+constexpr int kTraceSlots = 256;
+
+static cudaEvent_t* next_trace(tps_plan_s* P) {
+  if (!P->trace_ev) return nullptr;
+  const int slot = (int)(P->trace_count % P->trace_slots);
+  ++P->trace_count;
+  return P->trace_ev + 4 * slot;
+}
+
+// Defaults when the caller leaves a parameter at 0 and no predictor is asked
+// for.  Block size: 32 rows keeps the reduced system at n/16 rows while the
+// per-lane serial sweep stays short.
+static void default_params(const tps_plan_desc& d, int32_t& m, int32_t& mr, int32_t& S) {
+  if (m == 0) m = 32;
+  if (mr == 0) mr = 32;
+  if (S == 0) S = (d.residency == TPS_HOST_PINNED) ? 4 : 1;
+}
+
+extern "C" int tps_predict_params(const tps_plan_desc* desc, int32_t* m, int32_t* streams,
+                                  int64_t* chunk);
+
+static size_t workspace_for(const tps_plan_s* P, size_t* off_levels_out, size_t* off_dev_out) {
+  size_t off = 0;
+  off = align_up(off + 64);  // status word and refinement scalars
+  *off_levels_out = off;
+  std::vector<LevelPlan> lv;
+  const size_t eio = elem_bytes_io(P->desc.dtype);
+  const size_t ered = elem_bytes_red(P->desc.dtype);
+  int64_t nmax = P->desc.n_max;
+  size_t end = build_levels(nmax, P->m, P->m_reduced, eio, ered, off, lv);
+  if (P->desc.dtype == TPS_MIXED_F32_F64) {
+    // inner fp32 solve levels (reduced storage fp32) + residual and
+    // correction vectors (fp64) -- sized generously with fp64 elements
+    end = build_levels(nmax, P->m, P->m_reduced, 8, 8, off, lv);
+    end = align_up(end + (size_t)nmax * 8);  // r
+    end = align_up(end + (size_t)nmax * 8);  // delta
+  }
+  off = end;
+  *off_dev_out = off;
+  if (P->desc.residency == TPS_HOST_PINNED) {
+    for (int i = 0; i < 5; ++i) off = align_up(off + (size_t)nmax * eio);
+  }
+  return off;
+}
+
+}  // namespace tps
+
+using namespace tps;
+
+extern "C" {
+
+int tps_version(void) { return 100; }
+
+const char* tps_status_string(tps_status s) {
+  switch (s) {
+    case TPS_OK: return "ok";
+    case TPS_ERR_INVALID_ARG: return "invalid argument";
+    case TPS_ERR_UNSUPPORTED: return "unsupported";
+    case TPS_ERR_CUDA: return "CUDA runtime error";
+    case TPS_ERR_OOM: return "out of memory";
+    case TPS_ERR_ZERO_PIVOT: return "zero or non-finite pivot";
+    case TPS_ERR_NO_CONVERGENCE: return "refinement did not converge";
+    case TPS_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+tps_status tps_plan(const tps_plan_desc* desc, tps_plan_t* out) {
+  if (!out) return TPS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!desc) return TPS_ERR_INVALID_ARG;
+  const tps_plan_desc& d = *desc;
+  if (d.n_max < 0 || d.batch_max < 0 || d.reserved != 0) return TPS_ERR_INVALID_ARG;
+  if (d.dtype < TPS_F64 || d.dtype > TPS_F64_DF) return TPS_ERR_INVALID_ARG;
+  if (d.residency != TPS_DEVICE && d.residency != TPS_HOST_PINNED) return TPS_ERR_INVALID_ARG;
+  if (d.m != 0 && (d.m < 2 || d.m > (1 << 20))) return TPS_ERR_INVALID_ARG;
+  if (d.m_reduced != 0 && (d.m_reduced < 4 || d.m_reduced > (1 << 20))) return TPS_ERR_INVALID_ARG;
+  if (d.streams != 0 && (d.streams < 1 || d.streams > 32)) return TPS_ERR_INVALID_ARG;
+  if (d.chunk < 0 || d.max_iters < 0 || d.tol < 0.0) return TPS_ERR_INVALID_ARG;
+  if (d.flags & ~(TPS_TUNE_PREDICT | TPS_TUNE_EXHAUSTIVE | TPS_TRACE | TPS_EXTERNAL_WORKSPACE))
+    return TPS_ERR_INVALID_ARG;
+
+  tps_plan_s* P = new (std::nothrow) tps_plan_s();
+  if (!P) return TPS_ERR_OOM;
+  P->desc = d;
+  P->m = d.m;
+  P->m_reduced = d.m_reduced;
+  P->streams = d.streams;
+  P->chunk = d.chunk;
+  if (d.flags & TPS_TUNE_PREDICT) {
+    int32_t pm = 0, ps = 0;
+    int64_t pc = 0;
+    if (tps_predict_params(&d, &pm, &ps, &pc) == 0) {
+      if (P->m == 0) P->m = pm;
+      if (P->streams == 0) P->streams = ps;
+      if (P->chunk == 0) P->chunk = pc;
+    }
+  }
+  default_params(d, P->m, P->m_reduced, P->streams);
+
+  size_t off_levels = 0, off_dev = 0;
+  P->ws_needed = workspace_for(P, &off_levels, &off_dev);
+  P->off_levels = off_levels;
+
+  if (d.residency == TPS_HOST_PINNED) {
+    HostPipe* H = new (std::nothrow) HostPipe();
+    if (!H) { delete P; return TPS_ERR_OOM; }
+    P->pipe = H;
+    H->off_dev = off_dev;
+    cudaError_t e = cudaEventCreateWithFlags(&H->ev_start, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&H->ev_red, cudaEventDisableTiming);
+    for (int i = 0; i < P->streams && e == cudaSuccess; ++i) {
+      cudaStream_t s;
+      cudaEvent_t e1, e3;
+      e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+      if (e != cudaSuccess) break;
+      H->streams.push_back(s);
+      e = cudaEventCreateWithFlags(&e1, cudaEventDisableTiming);
+      if (e != cudaSuccess) break;
+      H->ev_done1.push_back(e1);
+      e = cudaEventCreateWithFlags(&e3, cudaEventDisableTiming);
+      if (e != cudaSuccess) break;
+      H->ev_done3.push_back(e3);
+    }
+    if (e != cudaSuccess) {
+      tps_plan_destroy(P);
+      return cuda_status(e);
+    }
+  }
+  if (d.flags & TPS_TRACE) {
+    P->trace_slots = kTraceSlots;
+    P->trace_ev = new (std::nothrow) cudaEvent_t[4 * kTraceSlots]();
+    if (!P->trace_ev) { tps_plan_destroy(P); return TPS_ERR_OOM; }
+    for (int i = 0; i < 4 * kTraceSlots; ++i) {
+      if (cudaEventCreate(&P->trace_ev[i]) != cudaSuccess) {
+        tps_plan_destroy(P);
+        return TPS_ERR_CUDA;
+      }
+    }
+  }
+  if (!(d.flags & TPS_EXTERNAL_WORKSPACE)) {
+    void* ws = nullptr;
+    cudaError_t e = cudaMalloc(&ws, P->ws_needed);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      tps_plan_destroy(P);
+      return TPS_ERR_OOM;
+    }
+    P->ws = (unsigned char*)ws;
+    P->ws_bytes = P->ws_needed;
+    P->ws_owned = true;
+    P->d_status = (int*)P->ws;
+    P->d_scalars = (double*)(P->ws + 8);
+    e = cudaMemset(P->ws, 0, 64);
+    if (e != cudaSuccess) {
+      tps_plan_destroy(P);
+      return TPS_ERR_CUDA;
+    }
+  }
+  *out = P;
+  return TPS_OK;
+}
+
+tps_status tps_plan_destroy(tps_plan_t P) {
+  if (!P) return TPS_ERR_INVALID_ARG;
+  if (P->pipe) {
+    HostPipe* H = P->pipe;
+    for (auto s : H->streams) cudaStreamDestroy(s);
+    for (auto e : H->ev_done1) cudaEventDestroy(e);
+    for (auto e : H->ev_done3) cudaEventDestroy(e);
+    if (H->ev_start) cudaEventDestroy(H->ev_start);
+    if (H->ev_red) cudaEventDestroy(H->ev_red);
+    delete H;
+  }
+  if (P->trace_ev) {
+    for (int i = 0; i < 4 * P->trace_slots; ++i)
+      if (P->trace_ev[i]) cudaEventDestroy(P->trace_ev[i]);
+    delete[] P->trace_ev;
+  }
+  if (P->ws_owned && P->ws) cudaFree(P->ws);
+  if (P->d_work) cudaFree(P->d_work);
+  delete P;
+  return TPS_OK;
+}
+
+tps_status tps_workspace_size(tps_plan_t P, size_t* bytes) {
+  if (!P || !bytes) return TPS_ERR_INVALID_ARG;
+  *bytes = P->ws_needed;
+  return TPS_OK;
+}
+
+tps_status tps_set_workspace(tps_plan_t P, void* dev_ptr, size_t bytes) {
+  if (!P || !dev_ptr) return TPS_ERR_INVALID_ARG;
+  if (!(P->desc.flags & TPS_EXTERNAL_WORKSPACE)) return TPS_ERR_INVALID_ARG;
+  if (bytes < P->ws_needed || ((uintptr_t)dev_ptr % kAlign) != 0) return TPS_ERR_INVALID_ARG;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, dev_ptr) != cudaSuccess ||
+      (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+    cudaGetLastError();
+    return TPS_ERR_INVALID_ARG;
+  }
+  P->ws = (unsigned char*)dev_ptr;
+  P->ws_bytes = bytes;
+  P->ws_owned = false;
+  P->d_status = (int*)P->ws;
+  P->d_scalars = (double*)(P->ws + 8);
+  return cudaMemset(P->ws, 0, 64) == cudaSuccess ? TPS_OK : TPS_ERR_CUDA;
+}
+
+}  // extern "C"
+
+namespace tps {
+
+// Device pointer check: device or managed memory, aligned to the element.
+static bool device_ptr_ok(const void* p, size_t align) {
+  if (!p || ((uintptr_t)p % align) != 0) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static bool host_pinned_ok(const void* p, size_t align) {
+  if (!p || ((uintptr_t)p % align) != 0) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
+static bool overlaps(const void* x, const void* y, size_t bytes) {
+  const uintptr_t a = (uintptr_t)x, b = (uintptr_t)y;
+  return a < b + bytes && b < a + bytes;
+}
+
+static tps_status check_solve_args(tps_plan_s* P, int64_t n, const void* a, const void* b,
+                                   const void* c, const void* d, void* x, bool host) {
+  if (!P) return TPS_ERR_INVALID_ARG;
+  if (n < 0 || n > P->desc.n_max) return TPS_ERR_INVALID_ARG;
+  if (!P->ws) return TPS_ERR_INVALID_ARG;  // external workspace not set
+  if (n == 0) return TPS_OK;
+  const size_t es = elem_bytes_io(P->desc.dtype);
+  const void* in[4] = {a, b, c, d};
+  for (const void* p : in) {
+    if (host ? !host_pinned_ok(p, es) : !device_ptr_ok(p, es)) return TPS_ERR_INVALID_ARG;
+    if (overlaps(p, x, (size_t)n * es)) return TPS_ERR_INVALID_ARG;
+  }
+  if (host ? !host_pinned_ok(x, es) : !device_ptr_ok(x, es)) return TPS_ERR_INVALID_ARG;
+  return TPS_OK;
+}
+
+}  // namespace tps
+
+extern "C" {
+
+tps_status tps_solve(tps_plan_t P, int64_t n, const void* a, const void* b, const void* c,
+                     const void* d, void* x, void* stream) {
+  tps_status st = check_solve_args(P, n, a, b, c, d, x, false);
+  if (st != TPS_OK || n == 0) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  P->last_stream = s;
+  if (P->desc.dtype == TPS_MIXED_F32_F64) return TPS_ERR_UNSUPPORTED;
+  std::vector<LevelPlan> lv;
+  build_levels(n, P->m, P->m_reduced, elem_bytes_io(P->desc.dtype),
+               elem_bytes_red(P->desc.dtype), P->off_levels, lv);
+  P->last_levels = (int32_t)lv.size();
+  return run_solve(P, n, a, b, c, d, x, s, lv, next_trace(P));
+}
+
+tps_status tps_solve_batched(tps_plan_t P, int64_t count, const int64_t* offsets,
+                             const int64_t* host_offsets, const void* a, const void* b,
+                             const void* c, const void* d, void* x, void* stream) {
+  (void)P; (void)count; (void)offsets; (void)host_offsets; (void)a; (void)b; (void)c; (void)d;
+  (void)x; (void)stream;
+  return TPS_ERR_UNSUPPORTED;
+}
+
+tps_status tps_solve_host_async(tps_plan_t P, int64_t n, const void* a, const void* b,
+                                const void* c, const void* d, void* x, void* stream) {
+  if (!P) return TPS_ERR_INVALID_ARG;
+  if (!P->pipe) return TPS_ERR_INVALID_ARG;  // plan not made for host residency
+  tps_status st = check_solve_args(P, n, a, b, c, d, x, true);
+  if (st != TPS_OK || n == 0) return st;
+  if (P->desc.dtype == TPS_MIXED_F32_F64) return TPS_ERR_UNSUPPORTED;
+  HostPipe* H = P->pipe;
+  cudaStream_t us = (cudaStream_t)stream;
+  const size_t es = elem_bytes_io(P->desc.dtype);
+  const size_t span = align_up((size_t)P->desc.n_max * es);
+  unsigned char* dev[5];
+  for (int i = 0; i < 5; ++i) dev[i] = P->ws + H->off_dev + i * span;
+  const unsigned char* host[5] = {(const unsigned char*)a, (const unsigned char*)b,
+                                  (const unsigned char*)c, (const unsigned char*)d,
+                                  (const unsigned char*)x};
+  std::vector<LevelPlan> lv;
+  build_levels(n, P->m, P->m_reduced, es, elem_bytes_red(P->desc.dtype), P->off_levels, lv);
+  P->last_levels = (int32_t)lv.size();
+  const int S = (int)H->streams.size();
+  cudaError_t e = cudaEventRecord(H->ev_start, us);
+  for (int i = 0; i < S && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(H->streams[i], H->ev_start, 0);
+  if (e != cudaSuccess) return TPS_ERR_CUDA;
+
+  if (lv.empty()) {  // small system: one stream, one chunk
+    cudaStream_t s0 = H->streams[0];
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+      e = cudaMemcpyAsync(dev[i], host[i], (size_t)n * es, cudaMemcpyHostToDevice, s0);
+    if (e == cudaSuccess) e = base_solve(P, n, dev[0], dev[1], dev[2], dev[3], dev[4], s0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync((void*)host[4], dev[4], (size_t)n * es, cudaMemcpyDeviceToHost, s0);
+    if (e == cudaSuccess) e = cudaEventRecord(H->ev_done3[0], s0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(us, H->ev_done3[0], 0);
+    P->last_stream = us;
+    return e == cudaSuccess ? TPS_OK : TPS_ERR_CUDA;
+  }
+
+  // chunks are runs of whole blocks; chunk j goes to stream j % S
+  const Level& L0 = lv[0].lv;
+  const int64_t rows_per_chunk = P->chunk > 0 ? P->chunk : (n + S - 1) / S;
+  int64_t bpc = rows_per_chunk / L0.m;
+  if (bpc < 1) bpc = 1;
+  const int64_t nch = (L0.p + bpc - 1) / bpc;
+  auto chunk_rows = [&](int64_t j, int64_t& kb, int64_t& ke, int64_t& r0, int64_t& r1) {
+    kb = j * bpc;
+    ke = kb + bpc < L0.p ? kb + bpc : L0.p;
+    r0 = kb * L0.m;
+    r1 = (ke == L0.p) ? n : ke * L0.m;
+  };
+  // Stage 1 per chunk, after its upload
+  for (int64_t j = 0; j < nch && e == cudaSuccess; ++j) {
+    cudaStream_t s = H->streams[j % S];
+    int64_t kb, ke, r0, r1;
+    chunk_rows(j, kb, ke, r0, r1);
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+      e = cudaMemcpyAsync(dev[i] + r0 * es, host[i] + r0 * es, (size_t)(r1 - r0) * es,
+                          cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = stage1_range(P, lv[0], kb, ke, dev[0], dev[1], dev[2], dev[3], s);
+  }
+  // join, Stage 2 on stream 0, fork
+  for (int i = 0; i < S && e == cudaSuccess; ++i) {
+    e = cudaEventRecord(H->ev_done1[i], H->streams[i]);
+    if (e == cudaSuccess && i > 0) e = cudaStreamWaitEvent(H->streams[0], H->ev_done1[i], 0);
+  }
+  if (e == cudaSuccess) e = reduced_solve(P, lv, H->streams[0]);
+  if (e == cudaSuccess) e = cudaEventRecord(H->ev_red, H->streams[0]);
+  for (int i = 1; i < S && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(H->streams[i], H->ev_red, 0);
+  // Stage 3 per chunk, then its download
+  for (int64_t j = 0; j < nch && e == cudaSuccess; ++j) {
+    cudaStream_t s = H->streams[j % S];
+    int64_t kb, ke, r0, r1;
+    chunk_rows(j, kb, ke, r0, r1);
+    e = stage3_range(P, lv[0], kb, ke, dev[0], dev[1], dev[2], dev[3], dev[4], s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync((void*)(host[4] + r0 * es), dev[4] + r0 * es, (size_t)(r1 - r0) * es,
+                          cudaMemcpyDeviceToHost, s);
+  }
+  for (int i = 0; i < S && e == cudaSuccess; ++i) {
+    e = cudaEventRecord(H->ev_done3[i], H->streams[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(us, H->ev_done3[i], 0);
+  }
+  P->last_stream = us;
+  return e == cudaSuccess ? TPS_OK : TPS_ERR_CUDA;
+}
+
+tps_status tps_plan_query(tps_plan_t P, tps_info* out) {
+  if (!P || !out) return TPS_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->m = P->m;
+  out->m_reduced = P->m_reduced;
+  out->streams = P->streams;
+  out->chunk = P->chunk;
+  out->levels = P->last_levels;
+  out->iterations = P->last_iters;
+  out->last_correction = P->last_corr;
+  out->workspace_bytes = P->ws_needed;
+  for (int i = 0; i < 4; ++i) out->stage_ms[i] = P->stage_ms[i];
+  if (!P->ws) return TPS_OK;
+  cudaStream_t s = P->last_stream;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return TPS_ERR_CUDA;
+  if (P->trace_ev && P->trace_count > 0) {
+    const int64_t cnt = P->trace_count < P->trace_slots ? P->trace_count : P->trace_slots;
+    double acc[4] = {0, 0, 0, 0};
+    for (int64_t i = 0; i < cnt; ++i) {
+      cudaEvent_t* ev = P->trace_ev + 4 * i;
+      float t;
+      if (cudaEventElapsedTime(&t, ev[0], ev[1]) == cudaSuccess) acc[0] += t;
+      if (cudaEventElapsedTime(&t, ev[1], ev[2]) == cudaSuccess) acc[1] += t;
+      if (cudaEventElapsedTime(&t, ev[2], ev[3]) == cudaSuccess) acc[2] += t;
+      if (cudaEventElapsedTime(&t, ev[0], ev[3]) == cudaSuccess) acc[3] += t;
+    }
+    cudaGetLastError();
+    for (int i = 0; i < 4; ++i) P->stage_ms[i] = (float)(acc[i] / cnt);
+    for (int i = 0; i < 4; ++i) out->stage_ms[i] = P->stage_ms[i];
+    P->trace_count = 0;
+  }
+  int word = 0;
+  if (cudaMemcpy(&word, P->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return TPS_ERR_CUDA;
+  if (cudaMemset(P->d_status, 0, sizeof(int)) != cudaSuccess) return TPS_ERR_CUDA;
+  int32_t status = TPS_OK;
+  if (word & ST_BAD_PIVOT) status = TPS_ERR_ZERO_PIVOT;
+  else if (word & ST_TIMEOUT) status = TPS_ERR_TIMEOUT;
+  else if ((word & ST_NO_CONVERGENCE) || P->host_status == TPS_ERR_NO_CONVERGENCE)
+    status = TPS_ERR_NO_CONVERGENCE;
+  P->host_status = TPS_OK;
+  out->status = status;
+  return TPS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// Host-side internals of libtps: the plan object, the level geometry of the
+// recursive partition solve, and the launch entry points of each
+// translation unit.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/tps.h"
+#include "partition_kernels.cuh"
+
+namespace tps {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// Rows per shared-memory chunk (and checkpoint spacing) for an element size.
+inline int chunk_rows(size_t elem_bytes) { return elem_bytes >= 8 ? 8 : 16; }
+constexpr int kWarpsPerCta = 4;
+
+// One level of the recursive solve: the system at this level has lv.n rows
+// and is split into lv.p blocks; its reduced system (2 lv.p rows) and the
+// Stage-1 checkpoints live in the workspace at the given offsets.
+struct LevelPlan {
+  Level lv;
+  int R;
+  size_t off_red[5];  // ra, rb, rc, rd, xr
+  size_t off_ck[3];   // gamma, y, v
+};
+
+// Block geometry for n rows and nominal block length m (m >= 2, n > m is
+// not required): p = ceil(n/m) blocks, a one-row tail merged into the block
+// before it so every block has >= 2 rows.
+Level make_level(int64_t n, int m, int R);
+
+// Levels of the recursive solve of an n-row system (empty when n fits the
+// one-warp base solve), with workspace offsets starting at `base`; returns
+// the end offset.
+size_t build_levels(int64_t n, int m0, int mr, size_t top_elem, size_t red_elem, size_t base,
+                    std::vector<LevelPlan>& out);
+
+struct HostPipe;  // streams and events of tps_solve_host_async
+
+}  // namespace tps
+
+struct tps_plan_s {
+  tps_plan_desc desc;
+  int32_t m = 0, m_reduced = 0, streams = 1;
+  int64_t chunk = 0;
+  unsigned char* ws = nullptr;
+  size_t ws_bytes = 0, ws_needed = 0;
+  bool ws_owned = false;
+  int* d_status = nullptr;     // device status word (first bytes of ws)
+  double* d_scalars = nullptr; // refinement reductions (next bytes of ws)
+  size_t off_levels = 0;       // first level buffer offset
+  cudaStream_t last_stream = nullptr;
+  int32_t last_levels = 0;
+  int32_t last_iters = 0;
+  double last_corr = 0.0;
+  float stage_ms[4] = {0, 0, 0, 0};
+  int32_t host_status = 0;     // numeric status found on the host (refinement)
+  tps::HostPipe* pipe = nullptr;
+  // TPS_TRACE: a ring of 4 events per solve (before/after Stage 1, after
+  // Stage 2, after Stage 3 of level 0), averaged by tps_plan_query
+  cudaEvent_t* trace_ev = nullptr;
+  int32_t trace_slots = 0;
+  int64_t trace_count = 0;
+  // batched work list (device) and its capacity in entries
+  void* d_work = nullptr;
+  size_t work_cap = 0;
+};
+
+namespace tps {
+
+// Enqueue the recursive partition solve of one device-resident system.
+// dtype selects the arithmetic; a..x are device pointers of the I/O type.
+// ev (optional, 4 events) is recorded before Stage 1, after Stage 1, after
+// Stage 2 and after Stage 3 of level 0.
+tps_status run_solve(tps_plan_s* P, int64_t n, const void* a, const void* b, const void* c,
+                     const void* d, void* x, cudaStream_t s, const std::vector<LevelPlan>& lv,
+                     cudaEvent_t* ev);
+
+// Level-0 pieces of the solve for the chunked host pipeline: Stage 1 and
+// Stage 3 on blocks [kb, ke), Stage 2 on the whole reduced system, and the
+// one-warp solve for n <= kBaseMax.
+cudaError_t stage1_range(tps_plan_s* P, const LevelPlan& L, int64_t kb, int64_t ke,
+                         const void* a, const void* b, const void* c, const void* d,
+                         cudaStream_t s);
+cudaError_t stage3_range(tps_plan_s* P, const LevelPlan& L, int64_t kb, int64_t ke,
+                         const void* a, const void* b, const void* c, const void* d, void* x,
+                         cudaStream_t s);
+cudaError_t reduced_solve(tps_plan_s* P, const std::vector<LevelPlan>& levels, cudaStream_t s);
+cudaError_t base_solve(tps_plan_s* P, int64_t n, const void* a, const void* b, const void* c,
+                       const void* d, void* x, cudaStream_t s);
+
+size_t elem_bytes_io(int dtype);
+size_t elem_bytes_red(int dtype);
+
+}  // namespace tps

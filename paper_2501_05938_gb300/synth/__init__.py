@@ -129,3 +129,56 @@ def offsets_from_sizes(sizes) -> np.ndarray:
 def to_f32(sys_: dict) -> dict:
     """The same system rounded to binary32 (d rounded too, not recomputed)."""
     return {k: np.asarray(v, dtype=np.float32) for k, v in sys_.items()}
+
+
+# ---------------------------------------------------------------------------
+# Device generator (synth.cu, built into libtpssynth.so): same arrays, made
+# on the GPU for the sizes the host would take too long on.
+# ---------------------------------------------------------------------------
+_dev_lib = None
+
+
+def _device_lib():
+    global _dev_lib
+    if _dev_lib is None:
+        import ctypes
+        import os
+
+        path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtpssynth.so")
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: run paper_2501_05938_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        L.tps_synth_system.argtypes = [ctypes.c_uint64, ctypes.c_int64, P, ctypes.c_int64,
+                                       ctypes.c_int, ctypes.c_double, P, P, P, P, P, P]
+        L.tps_synth_system.restype = ctypes.c_int
+        _dev_lib = L
+    return _dev_lib
+
+
+def system_device(seed: int, n: int, kind: int = KIND_PAPER, ratio: float = 2.0, offsets=None,
+                  device="cuda", stream=None):
+    """Like ``system`` but returns CUDA tensors made on the device.
+
+    ``offsets``: None, or an int64 tensor/array of count+1 entries."""
+    import ctypes
+
+    import torch
+
+    out = {k: torch.empty(n, dtype=torch.float64, device=device)
+           for k in ("a", "b", "c", "d", "x_true")}
+    off_t = None
+    count = 1
+    if offsets is not None:
+        off_t = torch.as_tensor(np.asarray(offsets, dtype=np.int64), device=device)
+        count = off_t.numel() - 1
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    st = _device_lib().tps_synth_system(
+        ctypes.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), n,
+        ctypes.c_void_p(off_t.data_ptr()) if off_t is not None else None, count, kind,
+        float(ratio), *[ctypes.c_void_p(out[k].data_ptr()) for k in ("a", "b", "c", "d", "x_true")],
+        ctypes.c_void_p(stream.cuda_stream))
+    if st != 0:
+        raise RuntimeError(f"tps_synth_system failed with {st}")
+    return out

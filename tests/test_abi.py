@@ -1,0 +1,68 @@
+"""The C ABI without a GPU: the library loads, exports every function
+include/tps.h declares, and rejects bad plan descriptors on the host."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2501_05938_gb300 import binding
+from paper_2501_05938_gb300 import build as tps_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    tps_build.build()
+    return binding.lib()
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b(tps_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert {"tps_plan", "tps_solve", "tps_solve_batched", "tps_solve_host_async"} <= names
+    for nm in names:
+        assert hasattr(lib, nm), nm
+    assert set(binding.EXPORTS) <= names
+
+
+def test_status_strings_and_version(lib):
+    assert binding.version() >= 100
+    assert binding.status_string(0) == "ok"
+    assert "pivot" in binding.status_string(5)
+    assert binding.status_string(99) == "unknown status"
+
+
+@pytest.mark.parametrize("field,value", [("n_max", -1), ("dtype", 7), ("residency", 3), ("m", 1),
+                                         ("m_reduced", 2), ("streams", 33), ("streams", -1),
+                                         ("chunk", -5), ("reserved", 1), ("flags", 1 << 10),
+                                         ("tol", -1.0)])
+def test_plan_rejects_bad_descriptors_on_the_host(lib, field, value):
+    d = binding.PlanDesc(n_max=1000, dtype=0)
+    setattr(d, field, value)
+    h = ctypes.c_void_p()
+    assert lib.tps_plan(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert not h.value
+
+
+def test_null_arguments(lib):
+    h = ctypes.c_void_p()
+    assert lib.tps_plan(None, ctypes.byref(h)) == 1
+    assert lib.tps_plan_destroy(None) == 1
+    assert lib.tps_solve(None, 10, None, None, None, None, None, None) == 1
+    assert lib.tps_solve_host_async(None, 10, None, None, None, None, None, None) == 1
+    assert lib.tps_plan_query(None, None) == 1
+    sz = ctypes.c_size_t()
+    assert lib.tps_workspace_size(None, ctypes.byref(sz)) == 1

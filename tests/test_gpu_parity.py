@@ -1,0 +1,223 @@
+"""GPU parity: libtps through its C ABI against the CPU oracle.
+
+Tolerances
+  fp64 paths (TPS_F64, TPS_F64_DF): relative forward error <= 1e-10 against
+  the fp64 Thomas oracle and relative residual <= 1e-12, the bar the solver
+  is specified to.  For these generators kappa_inf(A) <= 6, so a backward-
+  stable fp64 solve sits near 1e-15; the double-float path near 1e-13.
+  fp32 path (TPS_F32): against the fp64 oracle on the fp32-rounded inputs,
+  relative forward error <= 1e-5 and residual <= 1e-5 (kappa 6 times a few
+  hundred binary32 roundings of 6e-8).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2501_05938_gb300 import binding, synth
+
+pytestmark = pytest.mark.gpu
+
+F64_FWD, F64_RES = 1e-10, 1e-12
+F32_FWD, F32_RES = 1e-5, 1e-5
+
+
+def dev(v, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(v)).to(device="cuda", dtype=dtype)
+
+
+def run(plan, s, dtype=torch.float64):
+    a, b, c, d = (dev(s[k], dtype) for k in "abcd")
+    x = torch.empty_like(b)
+    plan.solve(a, b, c, d, x)
+    torch.cuda.synchronize()
+    return x.cpu().numpy().astype(np.float64), plan.query()
+
+
+def test_device_generator_is_bit_identical_to_numpy():
+    for n, off in ((100003, None), (5000, synth.offsets_from_sizes([1, 2, 3, 1000, 3994]))):
+        h = synth.system(1002, n, offsets=off)
+        g = synth.system_device(1002, n, offsets=off)
+        for k in ("a", "b", "c", "d", "x_true"):
+            np.testing.assert_array_equal(g[k].cpu().numpy(), h[k])
+        h = synth.system(77, n, kind=synth.KIND_RATIO, ratio=1.01, offsets=off)
+        g = synth.system_device(77, n, kind=synth.KIND_RATIO, ratio=1.01, offsets=off)
+        for k in ("a", "b", "c", "d", "x_true"):
+            np.testing.assert_array_equal(g[k].cpu().numpy(), h[k])
+
+
+CASES = [(1, 32), (2, 32), (3, 2), (63, 8), (64, 32), (65, 32), (65, 2), (100, 3), (1000, 10),
+         (4097, 8), (4096, 33), (65536, 256), (100003, 32), (100003, 1024), (262145, 64),
+         (1 << 20, 32), ((1 << 20) + 7, 100)]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f64_df"])
+@pytest.mark.parametrize("n,m", CASES)
+def test_fp64_paths_match_oracle(dtype, n, m):
+    s = synth.system(1000 + n, n)
+    plan = binding.Plan(n, dtype=dtype, m=m)
+    x, info = run(plan, s)
+    assert info["status"] == 0
+    ref = oracle.thomas(s["a"], s["b"], s["c"], s["d"])
+    fwd = oracle.rel_forward_error(x, ref)
+    res = oracle.rel_residual(s["a"], s["b"], s["c"], s["d"], x)
+    assert fwd <= F64_FWD, fwd
+    assert res <= F64_RES, res
+
+
+@pytest.mark.parametrize("n,m,mr", [(1 << 16, 256, 4), (1 << 18, 2, 8), (50000, 1000, 1000)])
+def test_reduced_block_sizes(n, m, mr):
+    s = synth.system(5 + n, n)
+    for dtype in ("f64", "f64_df"):
+        plan = binding.Plan(n, dtype=dtype, m=m, m_reduced=mr)
+        x, info = run(plan, s)
+        ref = oracle.thomas(s["a"], s["b"], s["c"], s["d"])
+        assert oracle.rel_forward_error(x, ref) <= F64_FWD
+        assert info["levels"] >= 1
+
+
+@pytest.mark.parametrize("n,m", [(65, 16), (4097, 16), (100003, 64), (1 << 20, 32)])
+def test_fp32_path_matches_oracle_on_rounded_inputs(n, m):
+    s64 = synth.system(2000 + n, n)
+    s32 = synth.to_f32(s64)
+    plan = binding.Plan(n, dtype="f32", m=m)
+    x, info = run(plan, s32, torch.float32)
+    assert info["status"] == 0
+    a, b, c, d = (s32[k].astype(np.float64) for k in "abcd")
+    ref = oracle.thomas(a, b, c, d)
+    assert oracle.rel_forward_error(x, ref) <= F32_FWD
+    assert oracle.rel_residual(a, b, c, d, x) <= F32_RES
+
+
+@pytest.mark.parametrize("ratio", [1.01, 1.1, 2.0])
+def test_weakly_dominant_systems(ratio):
+    n = 300001
+    s = synth.system(31, n, kind=synth.KIND_RATIO, ratio=ratio)
+    ref = oracle.thomas(s["a"], s["b"], s["c"], s["d"])
+    for dtype in ("f64", "f64_df"):
+        x, info = run(binding.Plan(n, dtype=dtype, m=64), s)
+        assert info["status"] == 0
+        assert oracle.rel_forward_error(x, ref) <= F64_FWD
+        assert oracle.rel_residual(s["a"], s["b"], s["c"], s["d"], x) <= F64_RES
+
+
+def test_zero_pivot_is_reported_not_raised():
+    n = 5000
+    s = synth.system(3, n)
+    s["b"][:] = 0.0
+    s["a"][:] = 0.0
+    s["c"][:] = 0.0
+    for dtype in ("f64", "f64_df"):
+        _, info = run(binding.Plan(n, dtype=dtype, m=32), s)
+        assert info["status_name"] == "TPS_ERR_ZERO_PIVOT"
+        # the word is cleared by the query
+        assert binding.Plan(n, dtype=dtype).query()["status"] == 0
+
+
+def test_invalid_arguments():
+    n = 1000
+    plan = binding.Plan(n, dtype="f64")
+    a = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+    b, c, d, x = (torch.ones(n + 1, dtype=torch.float64, device="cuda") for _ in range(4))
+    L = binding.lib()
+    st = binding._stream(None)
+    P = binding._ptr
+    # n above n_max
+    assert L.tps_solve(plan.handle, n + 1, P(a), P(b), P(c), P(d), P(x), st) == 1
+    # x aliases an input
+    assert L.tps_solve(plan.handle, n, P(a), P(b), P(c), P(d), P(a), st) == 1
+    # host (pageable) memory given to the device entry point
+    h = np.zeros(n)
+    hp = binding.ctypes.c_void_p(h.ctypes.data)
+    assert L.tps_solve(plan.handle, n, hp, P(b), P(c), P(d), P(x), st) == 1
+    # misaligned pointer
+    mis = binding.ctypes.c_void_p(a.data_ptr() + 4)
+    assert L.tps_solve(plan.handle, n, mis, P(b), P(c), P(d), P(x), st) == 1
+    # n = 0 is a no-op
+    assert L.tps_solve(plan.handle, 0, P(a), P(b), P(c), P(d), P(x), st) == 0
+
+
+def test_external_workspace():
+    n = 70000
+    s = synth.system(8, n)
+    plan = binding.Plan(n, dtype="f64_df", m=32, flags=binding.EXTERNAL_WORKSPACE)
+    need = plan.workspace_size()
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    plan.set_workspace(ws)
+    x, info = run(plan, s)
+    ref = oracle.thomas(s["a"], s["b"], s["c"], s["d"])
+    assert oracle.rel_forward_error(x, ref) <= F64_FWD
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("dtype", ["f64_df", "f64"])
+def test_full_size_single_system(dtype):
+    """n = 2^27 (the large single-system workload): every row against the
+    serial Thomas oracle run on the host."""
+    n = 1 << 27
+    g = synth.system_device(1002, n)
+    x = torch.empty_like(g["b"])
+    plan = binding.Plan(n, dtype=dtype, m=32)
+    plan.solve(g["a"], g["b"], g["c"], g["d"], x)
+    torch.cuda.synchronize()
+    assert plan.query()["status"] == 0
+    a, b, c, d = (g[k].cpu().numpy() for k in "abcd")
+    del g
+    ref = oracle.thomas(a, b, c, d)
+    xs = x.cpu().numpy()
+    assert oracle.rel_forward_error(xs, ref) <= F64_FWD
+    assert oracle.rel_residual(a, b, c, d, xs) <= F64_RES
+
+
+def pinned(v, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(v)).to(dtype).pin_memory()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f64_df"])
+@pytest.mark.parametrize("n,m,S,chunk", [(50, 32, 1, 0), (100003, 32, 1, 0), (100003, 32, 4, 0),
+                                          (100003, 64, 8, 5000), (262145, 32, 32, 0),
+                                          (262145, 1024, 3, 70000)])
+def test_host_pipeline_matches_oracle(dtype, n, m, S, chunk):
+    s = synth.system(4000 + n, n)
+    plan = binding.Plan(n, dtype=dtype, residency="host", m=m, streams=S, chunk=chunk)
+    a, b, c, d = (pinned(s[k]) for k in "abcd")
+    x = torch.empty(n, dtype=torch.float64).pin_memory()
+    stream = torch.cuda.Stream()
+    plan.solve_host_async(a, b, c, d, x, stream=stream)
+    stream.synchronize()
+    info = plan.query()
+    assert info["status"] == 0 and info["streams"] == S
+    ref = oracle.thomas(s["a"], s["b"], s["c"], s["d"])
+    xs = x.numpy()
+    assert oracle.rel_forward_error(xs, ref) <= F64_FWD
+    assert oracle.rel_residual(s["a"], s["b"], s["c"], s["d"], xs) <= F64_RES
+
+
+def test_host_pipeline_rejects_pageable_and_device_memory():
+    n = 1000
+    plan = binding.Plan(n, dtype="f64", residency="host", streams=2)
+    s = synth.system(1, n)
+    pg = [torch.as_tensor(s[k]) for k in "abcd"]  # pageable
+    x = torch.empty(n, dtype=torch.float64)
+    with pytest.raises(binding.TpsError):
+        plan.solve_host_async(*pg, x)
+    dv = [t.cuda() for t in pg]
+    with pytest.raises(binding.TpsError):
+        plan.solve_host_async(*dv, x.cuda())
+    # a device plan has no host pipeline
+    with pytest.raises(binding.TpsError):
+        binding.Plan(n, dtype="f64").solve_host_async(*[t.pin_memory() for t in pg],
+                                                       x.pin_memory())
+
+
+def test_trace_reports_stage_times():
+    n = 1 << 20
+    g = synth.system_device(9, n)
+    x = torch.empty_like(g["b"])
+    plan = binding.Plan(n, dtype="f64_df", m=32, flags=binding.TRACE)
+    for _ in range(3):
+        plan.solve(g["a"], g["b"], g["c"], g["d"], x)
+    info = plan.query()
+    s1, s2, s3, tot = info["stage_ms"]
+    assert s1 > 0 and s2 > 0 and s3 > 0 and tot >= s1 + s3
