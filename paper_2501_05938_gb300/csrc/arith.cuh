@@ -30,6 +30,7 @@ struct ArF64 {
   __device__ __forceinline__ static T zero() { return 0.0; }
   __device__ __forceinline__ static T one() { return 1.0; }
   __device__ __forceinline__ static T mul(T x, T y) { return x * y; }
+  __device__ __forceinline__ static T mul_nn(T x, T y) { return x * y; }
   // x - y*z, one rounding
   __device__ __forceinline__ static T sub_mul(T x, T y, T z) { return fma(-y, z, x); }
   __device__ __forceinline__ static T neg(T x) { return -x; }
@@ -44,11 +45,8 @@ struct ArF64 {
     e = fma(-x, r, 1.0);
     return fma(r, e, r);
   }
-  // true when x is zero, subnormal, infinite or NaN
-  __device__ __forceinline__ static bool bad_pivot(T x) {
-    const double ax = fabs(x);
-    return !(ax >= 2.2250738585072014e-308 && ax <= 1.7976931348623157e308);
-  }
+  // true when x is zero, subnormal or NaN
+  __device__ __forceinline__ static bool bad_pivot(T x) { return !(fabs(x) >= 2.2250738585072014e-308); }
   __device__ __forceinline__ static T from(double v) { return v; }
   __device__ __forceinline__ static T from(float v) { return (double)v; }
   __device__ __forceinline__ static void to(double& dst, T v) { dst = v; }
@@ -60,6 +58,7 @@ struct ArF32 {
   __device__ __forceinline__ static T zero() { return 0.0f; }
   __device__ __forceinline__ static T one() { return 1.0f; }
   __device__ __forceinline__ static T mul(T x, T y) { return __fmul_rn(x, y); }
+  __device__ __forceinline__ static T mul_nn(T x, T y) { return __fmul_rn(x, y); }
   __device__ __forceinline__ static T sub_mul(T x, T y, T z) { return fmaf(-y, z, x); }
   __device__ __forceinline__ static T neg(T x) { return -x; }
   // hardware reciprocal approximation refined by one Newton-Raphson step
@@ -68,10 +67,7 @@ struct ArF32 {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return fmaf(r, fmaf(-x, r, 1.0f), r);
   }
-  __device__ __forceinline__ static bool bad_pivot(T x) {
-    const float ax = fabsf(x);
-    return !(ax >= 1.17549435e-38f && ax <= 3.40282347e38f);
-  }
+  __device__ __forceinline__ static bool bad_pivot(T x) { return !(fabsf(x) >= 1.17549435e-38f); }
   __device__ __forceinline__ static T from(float v) { return v; }
   __device__ __forceinline__ static void to(float& dst, T v) { dst = v; }
 };
@@ -137,6 +133,16 @@ struct ArDF {
     fast_two_sum(p, e, r.hi, r.lo);
     return r;
   }
+  // x*y left as the unevaluated pair (p, e), |e| <= ~2^-22 |p|: for a product
+  // that only feeds sub_mul / mul (which accept such pairs); recurrences
+  // renormalise through mul or sub_mul every step.
+  __device__ __forceinline__ static T mul_nn(T x, T y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    return {p, e};
+  }
   // x - y*z: the product is formed as an unevaluated pair (p, pe), then
   // TwoSum of the high parts and a final Fast2Sum.
   __device__ __forceinline__ static T sub_mul(T x, T y, T z) {
@@ -164,10 +170,7 @@ struct ArDF {
     fast_two_sum(r, __fmul_rn(r, fmaf(e, e, e)), out.hi, out.lo);
     return out;
   }
-  __device__ __forceinline__ static bool bad_pivot(T x) {
-    const float ax = fabsf(x.hi);
-    return !(ax >= 1.17549435e-38f && ax <= 3.40282347e38f);
-  }
+  __device__ __forceinline__ static bool bad_pivot(T x) { return !(fabsf(x.hi) >= 1.17549435e-38f); }
   __device__ __forceinline__ static T from(double v) { return df_split(v); }
   __device__ __forceinline__ static T from(float2 v) { return {v.x, v.y}; }
   __device__ __forceinline__ static void to(double& dst, T v) {

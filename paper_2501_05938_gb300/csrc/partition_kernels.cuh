@@ -7,16 +7,21 @@
 // block, whose length Llast lies in [2, m + 1] (a one-row tail is merged into
 // the block before it).  The first and last row of each block are its
 // interface unknowns f_k and l_k; the reduced system in (f_0, l_0, f_1, ...)
-// is tridiagonal, so row 2k is block k's "first" equation in
-// (l_{k-1}, f_k, l_k) and row 2k+1 its "last" equation in (f_k, l_k, f_{k+1}).
+// is tridiagonal: row 2k is block k's "first" equation in (l_{k-1}, f_k, l_k)
+// and row 2k+1 its "last" equation in (f_k, l_k, f_{k+1}).
 //
 // GPU mapping.  One lane owns one block and sweeps it serially (the
-// recurrences are first-order); a warp owns 32 consecutive blocks.  The warp
-// streams its blocks in chunks of R rows: for each of a, b, c, d it copies
-// 32 blocks x R rows into shared memory with cp.async (each block's R rows
-// are contiguous in global memory, so the copies coalesce), double
-// buffered, with a padded stride of R+1 elements per block so that lane j
-// reading row r of block j hits distinct banks.
+// recurrences are first-order); a warp owns 32 consecutive blocks and a CTA
+// W warps.  The warp streams its blocks through shared memory in chunks of R
+// rows, double buffered: for each of a, b, c, d the warp copies the chunk's
+// rows of its 32 blocks with cp.async in 16-byte pieces, consecutive lanes
+// taking consecutive pieces of one block (64 contiguous bytes per block for
+// fp64), so each copy instruction moves 512 coalesced bytes.  Per-lane piece
+// offsets are computed once per kernel.  In shared memory each block's rows
+// sit in a slot padded to R + 16/sizeof(element) elements, so the 128-bit
+// loads with which a lane reads its own block hit distinct banks across a
+// quarter-warp.  Where pointers are not 16-byte aligned (or m is not a
+// multiple of the 16-byte vector) the same copies go element by element.
 //
 // Stage 1 is a single top-down sweep per block.  Writing the interior
 // relation after row j as  beta_j x_j + c_j x_{j+1} = g_j - alpha_j f  (a
@@ -25,15 +30,15 @@
 // (f_k, l_k, f_{k+1}).  The first reduced equation needs the first interior
 // unknown as a function of f_k and l_k; instead of a second, bottom-up
 // sweep, the sweep carries x_1 = P - Q f - S x_{j+1} along, which costs four
-// multiply-adds per row and no extra reciprocal.  Every K = R rows the
-// normalised relation x_j = (g_j - alpha_j f - c_j x_{j+1}) / beta_j is
+// multiply-adds per row and no extra reciprocal.  At every chunk boundary
+// the normalised relation x_j = (g_j - alpha_j f - c_j x_{j+1}) / beta_j is
 // written out as a checkpoint (c/beta, g/beta, alpha/beta).
 //
 // Stage 3 walks each block's chunks bottom-up.  A chunk restarts the forward
 // elimination from its checkpoint (with f now known), keeps the R pivots and
 // right-hand sides in registers, and back-substitutes from the x of the row
-// below it (l_k for the last chunk).  The result goes through the chunk's
-// shared-memory slots so the stores coalesce like the loads.
+// below it (l_k for the last chunk).  The chunk's x goes back through the
+// shared-memory slots and out with the same coalesced piece mapping.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -41,23 +46,6 @@
 #include "arith.cuh"
 
 namespace tps {
-
-// ------------------------------------------------------------------ cp.async
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* smem_dst, const void* gmem_src) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  if constexpr (BYTES == 8) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
-  } else {
-    static_assert(BYTES == 4, "cp.async size");
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
-  }
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
 
 // ------------------------------------------------------------------ geometry
 struct Level {
@@ -78,50 +66,137 @@ __device__ __forceinline__ int block_len(const Level& lv, int64_t k) {
 // Status bits written into the device status word.
 enum : int { ST_BAD_PIVOT = 1, ST_NO_CONVERGENCE = 2, ST_TIMEOUT = 4 };
 
+// ------------------------------------------------------------------ cp.async
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem_dst, const void* gmem_src) {
+  const uint32_t s = smem_u32(smem_dst);
+  if constexpr (BYTES == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+  } else if constexpr (BYTES == 8) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+  } else {
+    static_assert(BYTES == 4, "cp.async size");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
+  }
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// ------------------------------------------------------------------ warp tile
 template <class Tin, int R>
-struct WarpTile {
-  static constexpr int kStride = R + 1;                 // padded row stride per block
-  static constexpr int kArr = 32 * kStride;             // one array of the chunk
-  static constexpr int kBuf = 4 * kArr;                 // a, b, c, d
-  static constexpr int kWarp = 2 * kBuf;                // double buffered
-  static constexpr size_t kBytesPerWarp = sizeof(Tin) * kWarp;
+struct Tile {
+  static constexpr int kVec = 16 / (int)sizeof(Tin);  // elements per 16-byte piece
+  static_assert(R % kVec == 0, "chunk rows must fill 16-byte pieces");
+  static constexpr int kPieces = R / kVec;            // pieces per block and chunk
+  static constexpr int kStride = R + kVec;            // padded block slot (16-byte multiple)
+  static constexpr int kArr = 32 * kStride;           // one array of one buffer
+  static constexpr int kBuf = 4 * kArr;               // a, b, c, d
+  static constexpr size_t kBytesPerWarp = sizeof(Tin) * 2 * kBuf;
 };
 
-// Copy rows [row0, row0 + R) of the warp's blocks (clipped to each block's
-// length) of the four arrays into one buffer.  Lane l copies elements
-// e = l + 32 j, e -> (block e / R, row e % R), so consecutive lanes read
-// consecutive rows of one block.
+// 16 bytes of consecutive rows (one 128-bit shared access).
+template <class Tin>
+struct Vec16 {
+  Tin v[16 / sizeof(Tin)];
+};
+template <class Tin>
+__device__ __forceinline__ Vec16<Tin> lds16(const Tin* p) {
+  Vec16<Tin> r;
+  *reinterpret_cast<float4*>(&r) = *reinterpret_cast<const float4*>(p);
+  return r;
+}
+
+// The pieces lane `lane` copies for every array: piece q = lane + 32 j
+// (j < kPieces) is piece q % kPieces of block q / kPieces of the warp.
 template <class Tin, int R>
-__device__ __forceinline__ void load_chunk(Tin* buf, const Tin* __restrict__ a,
-                                           const Tin* __restrict__ b, const Tin* __restrict__ c,
-                                           const Tin* __restrict__ d, const Level& lv, int64_t k0,
-                                           int nb, int row0, int lane) {
-  using WT = WarpTile<Tin, R>;
+struct PieceMap {
+  using TL = Tile<Tin, R>;
+  int64_t goff[TL::kPieces];  // element offset of the piece in the arrays (chunk 0)
+  int soff[TL::kPieces];      // element offset in a buffer's array
+  int row[TL::kPieces];       // first row of the piece within its block (chunk 0)
+  int len[TL::kPieces];       // length of the piece's block, 0 past the last block
+  __device__ __forceinline__ void init(const Level& lv, int64_t k0, int nb, int lane);
+};
+
+template <class Tin, int R>
+__device__ __forceinline__ void PieceMap<Tin, R>::init(const Level& lv, int64_t k0, int nb,
+                                                       int lane) {
 #pragma unroll
-  for (int j = 0; j < R; ++j) {
-    const int e = lane + 32 * j;
-    const int blk = e / R;
-    const int r = e % R;
-    const int row = row0 + r;
-    if (blk < nb && row < block_len(lv, k0 + blk)) {
-      const int64_t g = (k0 + blk) * (int64_t)lv.m + row;
-      const int s = blk * WT::kStride + r;
-      cp_async<sizeof(Tin)>(buf + 0 * WT::kArr + s, a + g);
-      cp_async<sizeof(Tin)>(buf + 1 * WT::kArr + s, b + g);
-      cp_async<sizeof(Tin)>(buf + 2 * WT::kArr + s, c + g);
-      cp_async<sizeof(Tin)>(buf + 3 * WT::kArr + s, d + g);
+  for (int j = 0; j < TL::kPieces; ++j) {
+    const int q = lane + 32 * j;
+    const int blk = q / TL::kPieces;
+    const int pc = q % TL::kPieces;
+    row[j] = pc * TL::kVec;
+    len[j] = blk < nb ? block_len(lv, k0 + blk) : 0;
+    goff[j] = (k0 + blk) * (int64_t)lv.m + row[j];
+    soff[j] = blk * TL::kStride + row[j];
+  }
+}
+
+// Copy rows [row0, row0 + R) of the warp's blocks (clipped to each block's
+// length) of src[0..n_arr) into the buffer's arrays.  kVec16: whole pieces
+// go as one 16-byte copy (arrays 16-byte aligned, m a multiple of kVec);
+// otherwise, and for a block's ragged last piece, element by element.
+template <class Tin, int R, bool kVec16>
+__device__ __forceinline__ void load_chunk(Tin* buf, const Tin* const* src, int n_arr,
+                                           const PieceMap<Tin, R>& pm, int row0) {
+  using TL = Tile<Tin, R>;
+#pragma unroll
+  for (int j = 0; j < TL::kPieces; ++j) {
+    const int avail = pm.len[j] - (row0 + pm.row[j]);  // rows of this piece in its block
+    const int64_t g = pm.goff[j] + row0;
+    if (kVec16 && avail >= TL::kVec) {
+      for (int t = 0; t < n_arr; ++t) cp_async<16>(buf + t * TL::kArr + pm.soff[j], src[t] + g);
+    } else if (avail > 0) {
+#pragma unroll
+      for (int v = 0; v < TL::kVec; ++v)
+        if (v < avail)
+          for (int t = 0; t < n_arr; ++t)
+            cp_async<sizeof(Tin)>(buf + t * TL::kArr + pm.soff[j] + v, src[t] + g + v);
     }
   }
 }
 
+// Write rows [row0, row0 + R) of the warp's blocks from the buffer's first
+// array to x (same piece mapping as the loads).
+template <class Tin, int R, bool kVec16>
+__device__ __forceinline__ void store_chunk(Tin* __restrict__ x, const Tin* buf,
+                                            const PieceMap<Tin, R>& pm, int row0) {
+  using TL = Tile<Tin, R>;
+#pragma unroll
+  for (int j = 0; j < TL::kPieces; ++j) {
+    const int avail = pm.len[j] - (row0 + pm.row[j]);
+    const int64_t g = pm.goff[j] + row0;
+    if (kVec16 && avail >= TL::kVec) {
+      *reinterpret_cast<float4*>(x + g) = *reinterpret_cast<const float4*>(buf + pm.soff[j]);
+    } else if (avail > 0) {
+#pragma unroll
+      for (int v = 0; v < TL::kVec; ++v)
+        if (v < avail) x[g + v] = buf[pm.soff[j] + v];
+    }
+  }
+}
+
+// chunks the warp iterates: the longest block of the warp decides
 __device__ __forceinline__ int warp_chunks(const Level& lv, int64_t k0, int nb, int R) {
-  // only the warp holding block p-1 can have a block longer than m
   const int lmax = (k0 + nb == lv.p) ? max(lv.m, lv.llast) : lv.m;
   return (lmax + R - 1) / R;
 }
+// shortest block among the warp's active lanes
+__device__ __forceinline__ int warp_lmin(const Level& lv, int64_t k0, int nb) {
+  return (k0 + nb == lv.p) ? min(lv.m, lv.llast) : lv.m;
+}
 
 // ------------------------------------------------------------------ Stage 1
-template <class Ar, class Tin, class Tred, int R, int W>
+template <class Ar, class Tin, class Tred, int R, int W, bool kVec16>
 __global__ void __launch_bounds__(W * 32)
     k_stage1(Level lv, const Tin* __restrict__ a, const Tin* __restrict__ b,
              const Tin* __restrict__ c, const Tin* __restrict__ d, Tred* __restrict__ ra,
@@ -129,17 +204,25 @@ __global__ void __launch_bounds__(W * 32)
              Tred* __restrict__ ck_gam, Tred* __restrict__ ck_y, Tred* __restrict__ ck_v,
              int* __restrict__ status) {
   using T = typename Ar::T;
-  using WT = WarpTile<Tin, R>;
+  using TL = Tile<Tin, R>;
+  constexpr int V = TL::kVec;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t k0 = lv.k_begin + ((int64_t)blockIdx.x * W + warp) * 32;
   if (k0 >= lv.k_end) return;
   const int nb = (int)(lv.k_end - k0 < 32 ? lv.k_end - k0 : 32);
-  Tin* tile = reinterpret_cast<Tin*>(smem_raw) + warp * WT::kWarp;
   const int64_t k = k0 + lane;
   const bool active = lane < nb;
   const int L = active ? block_len(lv, k) : 0;
   const int nch = warp_chunks(lv, k0, nb, R);
+  const int lmin = warp_lmin(lv, k0, nb);
+
+  Tin* tile = reinterpret_cast<Tin*>(smem_raw) + warp * 2 * TL::kBuf;
+  const Tin* const srcs[4] = {a, b, c, d};
+  PieceMap<Tin, R> pm;
+  pm.init(lv, k0, nb, lane);
+  load_chunk<Tin, R, kVec16>(tile, srcs, 4, pm, 0);
+  cp_async_commit();
 
   // virtual state before row 1 (relation x_0 = f): rbeta = 1, c_prev = 0,
   // g = 0, alpha = -1; first interior unknown x_1 = P - Q f - S x_1 with
@@ -150,53 +233,68 @@ __global__ void __launch_bounds__(W * 32)
   T beta = Ar::one(), clast = Ar::zero();
   bool bad = false;
 
-  load_chunk<Tin, R>(tile, a, b, c, d, lv, k0, nb, 0, lane);
-  cp_async_commit();
+  // one interior row (1 <= row <= L-2)
+  auto interior = [&](const T av, const T bv, const T cv, const T dv) {
+    const T ratio = Ar::mul_nn(av, rbp);
+    beta = Ar::sub_mul(bv, ratio, cprev);
+    g = Ar::sub_mul(dv, ratio, g);
+    al = Ar::neg(Ar::mul(ratio, al));
+    bad |= Ar::bad_pivot(beta);
+    const T rbeta = Ar::rcp(beta);
+    const T tt = Ar::mul_nn(S, rbeta);
+    P = Ar::sub_mul(P, tt, g);
+    Q = Ar::sub_mul(Q, tt, al);
+    S = Ar::neg(Ar::mul(tt, cv));
+    rbp = rbeta;
+    cprev = cv;
+  };
+
   for (int ch = 0; ch < nch; ++ch) {
-    if (ch + 1 < nch)
-      load_chunk<Tin, R>(tile + ((ch + 1) & 1) * WT::kBuf, a, b, c, d, lv, k0, nb, (ch + 1) * R,
-                         lane);
+    const int row0 = ch * R;
+    if (ch + 1 < nch) load_chunk<Tin, R, kVec16>(tile + ((ch + 1) & 1) * TL::kBuf, srcs, 4, pm, row0 + R);
     cp_async_commit();
     cp_async_wait<1>();
     __syncwarp();
-    const Tin* t = tile + (ch & 1) * WT::kBuf + lane * WT::kStride;
+    const Tin* t = tile + (ch & 1) * TL::kBuf + lane * TL::kStride;
+    const bool fast = ch >= 1 && row0 + R <= lmin - 1;
+    if (fast) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int row = ch * R + r;
-      if (row < L) {
-        const T av = Ar::from(t[0 * WT::kArr + r]);
-        const T bv = Ar::from(t[1 * WT::kArr + r]);
-        const T cv = Ar::from(t[2 * WT::kArr + r]);
-        const T dv = Ar::from(t[3 * WT::kArr + r]);
-        if (row == 0) {
-          a0 = av; b0 = bv; c0 = cv; d0 = dv;
-        } else {
-          const T ratio = Ar::mul(av, rbp);
-          beta = Ar::sub_mul(bv, ratio, cprev);
-          g = Ar::sub_mul(dv, ratio, g);
-          al = Ar::neg(Ar::mul(ratio, al));
-          if (row < L - 1) {
-            bad |= Ar::bad_pivot(beta);
-            const T rbeta = Ar::rcp(beta);
-            const T tt = Ar::mul(S, rbeta);
-            P = Ar::sub_mul(P, tt, g);
-            Q = Ar::sub_mul(Q, tt, al);
-            S = Ar::neg(Ar::mul(tt, cv));
-            rbp = rbeta;
-            cprev = cv;
-            if (((row + 1) % R) == 0 && row <= L - 3) {
-              const int64_t slot = (int64_t)((row + 1) / R - 1) * lv.p + k;
-              Ar::to(ck_gam[slot], Ar::mul(cv, rbeta));
-              Ar::to(ck_y[slot], Ar::mul(g, rbeta));
-              Ar::to(ck_v[slot], Ar::mul(al, rbeta));
-            }
+      for (int r = 0; r < R; r += V) {
+        const Vec16<Tin> xa = lds16(t + r), xb = lds16(t + TL::kArr + r),
+                         xc = lds16(t + 2 * TL::kArr + r), xd = lds16(t + 3 * TL::kArr + r);
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+          interior(Ar::from(xa.v[v]), Ar::from(xb.v[v]), Ar::from(xc.v[v]), Ar::from(xd.v[v]));
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int row = row0 + r;
+        if (row < L) {
+          const T av = Ar::from(t[r]), bv = Ar::from(t[TL::kArr + r]);
+          const T cv = Ar::from(t[2 * TL::kArr + r]), dv = Ar::from(t[3 * TL::kArr + r]);
+          if (row == 0) {
+            a0 = av; b0 = bv; c0 = cv; d0 = dv;
+          } else if (row < L - 1) {
+            interior(av, bv, cv, dv);
           } else {
+            const T ratio = Ar::mul_nn(av, rbp);
+            beta = Ar::sub_mul(bv, ratio, cprev);
+            g = Ar::sub_mul(dv, ratio, g);
+            al = Ar::neg(Ar::mul(ratio, al));
             clast = cv;
           }
         }
       }
     }
-    __syncwarp();
+    // checkpoint after the chunk's last row, when the next chunk has interior rows
+    if (active && row0 + R <= L - 2) {
+      const int64_t slot = (int64_t)ch * lv.p + k;
+      Ar::to(ck_gam[slot], Ar::mul(cprev, rbp));
+      Ar::to(ck_y[slot], Ar::mul(g, rbp));
+      Ar::to(ck_v[slot], Ar::mul(al, rbp));
+    }
+    __syncwarp();  // the buffer is refilled by the next iteration's copies
   }
   if (active) {
     bad |= Ar::bad_pivot(beta);
@@ -215,24 +313,32 @@ __global__ void __launch_bounds__(W * 32)
 }
 
 // ------------------------------------------------------------------ Stage 3
-template <class Ar, class Tin, class Tred, int R, int W>
+template <class Ar, class Tin, class Tred, int R, int W, bool kVec16>
 __global__ void __launch_bounds__(W * 32)
     k_stage3(Level lv, const Tin* __restrict__ a, const Tin* __restrict__ b,
              const Tin* __restrict__ c, const Tin* __restrict__ d, const Tred* __restrict__ xred,
              const Tred* __restrict__ ck_gam, const Tred* __restrict__ ck_y,
              const Tred* __restrict__ ck_v, Tin* __restrict__ x, int* __restrict__ status) {
   using T = typename Ar::T;
-  using WT = WarpTile<Tin, R>;
+  using TL = Tile<Tin, R>;
+  constexpr int V = TL::kVec;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t k0 = lv.k_begin + ((int64_t)blockIdx.x * W + warp) * 32;
   if (k0 >= lv.k_end) return;
   const int nb = (int)(lv.k_end - k0 < 32 ? lv.k_end - k0 : 32);
-  Tin* tile = reinterpret_cast<Tin*>(smem_raw) + warp * WT::kWarp;
   const int64_t k = k0 + lane;
   const bool active = lane < nb;
   const int L = active ? block_len(lv, k) : 0;
   const int nch = warp_chunks(lv, k0, nb, R);
+  const int lmin = warp_lmin(lv, k0, nb);
+
+  Tin* tile = reinterpret_cast<Tin*>(smem_raw) + warp * 2 * TL::kBuf;
+  const Tin* const srcs[4] = {a, b, c, d};
+  PieceMap<Tin, R> pm;
+  pm.init(lv, k0, nb, lane);
+  load_chunk<Tin, R, kVec16>(tile, srcs, 4, pm, (nch - 1) * R);
+  cp_async_commit();
 
   T f = Ar::zero(), l = Ar::zero();
   if (active) {
@@ -242,78 +348,94 @@ __global__ void __launch_bounds__(W * 32)
   T xnext = l;  // x of the row below the chunk being processed
   bool bad = false;
 
-  // chunks bottom-up: ch = nch-1 .. 0, buffer parity by visiting order
-  load_chunk<Tin, R>(tile, a, b, c, d, lv, k0, nb, (nch - 1) * R, lane);
-  cp_async_commit();
+  // chunks bottom-up: ch = nch-1 .. 0; buffer parity follows the visiting order
   for (int it = 0; it < nch; ++it) {
     const int ch = nch - 1 - it;
-    if (ch > 0)
-      load_chunk<Tin, R>(tile + ((it + 1) & 1) * WT::kBuf, a, b, c, d, lv, k0, nb, (ch - 1) * R,
-                         lane);
+    const int row0 = ch * R;
+    if (ch > 0) load_chunk<Tin, R, kVec16>(tile + ((it + 1) & 1) * TL::kBuf, srcs, 4, pm, row0 - R);
     cp_async_commit();
     cp_async_wait<1>();
     __syncwarp();
-    Tin* t = tile + (it & 1) * WT::kBuf + lane * WT::kStride;
+    Tin* tb = tile + (it & 1) * TL::kBuf;
+    Tin* t = tb + lane * TL::kStride;
 
     // relation entering the chunk: x_{row0-1} = zp - gp * x_{row0}
     T zp = f, gp = Ar::zero();
-    if (active && ch > 0 && ch * R <= L - 2) {
+    if (active && ch > 0 && row0 <= L - 2) {
       const int64_t slot = (int64_t)(ch - 1) * lv.p + k;
       gp = Ar::from(ck_gam[slot]);
       zp = Ar::sub_mul(Ar::from(ck_y[slot]), Ar::from(ck_v[slot]), f);
     }
     T Z[R], G[R];
+    Tin xo[R];
+    const bool fast = ch >= 1 && row0 + R <= lmin - 1;
+    if (fast) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int row = ch * R + r;
-      Z[r] = Ar::zero();
-      G[r] = Ar::zero();
-      if (row >= 1 && row <= L - 2) {
-        const T av = Ar::from(t[0 * WT::kArr + r]);
-        const T bv = Ar::from(t[1 * WT::kArr + r]);
-        const T cv = Ar::from(t[2 * WT::kArr + r]);
-        const T dv = Ar::from(t[3 * WT::kArr + r]);
-        const T beta = Ar::sub_mul(bv, av, gp);
-        bad |= Ar::bad_pivot(beta);
-        const T rbeta = Ar::rcp(beta);
-        zp = Ar::mul(Ar::sub_mul(dv, av, zp), rbeta);
-        gp = Ar::mul(cv, rbeta);
-        Z[r] = zp;
-        G[r] = gp;
-      }
-    }
+      for (int r = 0; r < R; r += V) {
+        const Vec16<Tin> xa = lds16(t + r), xb = lds16(t + TL::kArr + r),
+                         xc = lds16(t + 2 * TL::kArr + r), xd = lds16(t + 3 * TL::kArr + r);
 #pragma unroll
-    for (int r = R - 1; r >= 0; --r) {
-      const int row = ch * R + r;
-      if (row < L) {
-        T xr;
-        if (row == L - 1) {
-          xr = l;
-        } else if (row == 0) {
-          xr = f;
-        } else {
-          xr = Ar::sub_mul(Z[r], G[r], xnext);
-          xnext = xr;
+        for (int v = 0; v < V; ++v) {
+          const T av = Ar::from(xa.v[v]);
+          const T beta = Ar::sub_mul(Ar::from(xb.v[v]), av, gp);
+          bad |= Ar::bad_pivot(beta);
+          const T rbeta = Ar::rcp(beta);
+          zp = Ar::mul_nn(Ar::sub_mul(Ar::from(xd.v[v]), av, zp), rbeta);
+          gp = Ar::mul_nn(Ar::from(xc.v[v]), rbeta);
+          Z[r + v] = zp;
+          G[r + v] = gp;
         }
-        Ar::to(t[0 * WT::kArr + r], xr);  // a is no longer needed: reuse its slot
       }
-    }
-    __syncwarp();
-    // coalesced write-back of the chunk's x, same element mapping as the load
-    {
-      const Tin* tx = tile + (it & 1) * WT::kBuf;
-      const int row0 = ch * R;
 #pragma unroll
-      for (int j = 0; j < R; ++j) {
-        const int e = lane + 32 * j;
-        const int blk = e / R;
-        const int r = e % R;
+      for (int r = R - 1; r >= 0; --r) {
+        xnext = Ar::sub_mul(Z[r], G[r], xnext);
+        Ar::to(xo[r], xnext);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
         const int row = row0 + r;
-        if (blk < nb && row < block_len(lv, k0 + blk))
-          x[(k0 + blk) * (int64_t)lv.m + row] = tx[blk * WT::kStride + r];
+        Z[r] = Ar::zero();
+        G[r] = Ar::zero();
+        if (row >= 1 && row <= L - 2) {
+          const T av = Ar::from(t[r]);
+          const T beta = Ar::sub_mul(Ar::from(t[TL::kArr + r]), av, gp);
+          bad |= Ar::bad_pivot(beta);
+          const T rbeta = Ar::rcp(beta);
+          zp = Ar::mul_nn(Ar::sub_mul(Ar::from(t[3 * TL::kArr + r]), av, zp), rbeta);
+          gp = Ar::mul_nn(Ar::from(t[2 * TL::kArr + r]), rbeta);
+          Z[r] = zp;
+          G[r] = gp;
+        }
+      }
+#pragma unroll
+      for (int r = R - 1; r >= 0; --r) {
+        const int row = row0 + r;
+        T xr = Ar::zero();
+        if (row < L) {
+          if (row == L - 1) {
+            xr = l;
+          } else if (row == 0) {
+            xr = f;
+          } else {
+            xr = Ar::sub_mul(Z[r], G[r], xnext);
+            xnext = xr;
+          }
+        }
+        Ar::to(xo[r], xr);
       }
     }
+    // x of the chunk into the lane's a slot (no longer needed), then out
+#pragma unroll
+    for (int r = 0; r < R; r += V) {
+      Vec16<Tin> w;
+#pragma unroll
+      for (int v = 0; v < V; ++v) w.v[v] = xo[r + v];
+      *reinterpret_cast<float4*>(t + r) = *reinterpret_cast<const float4*>(&w);
+    }
     __syncwarp();
+    store_chunk<Tin, R, kVec16>(x, tb, pm, row0);
+    __syncwarp();  // the buffer is refilled by the next iteration's copies
   }
   if (active && bad) atomicOr(status, ST_BAD_PIVOT);
 }

@@ -63,24 +63,49 @@ size_t elem_bytes_io(int dtype) { return dtype == TPS_F32 ? 4 : 8; }
 size_t elem_bytes_red(int dtype) { return dtype == TPS_F32 ? 4 : 8; }
 
 // ------------------------------------------------------------------ launchers
+// 16-byte copies need 16-byte aligned arrays and blocks that start on a
+// 16-byte boundary (m a multiple of the 16-byte vector); otherwise the
+// kernels copy element by element.
+template <class Tin>
+static bool vec16_ok(int m, const void* const* ptrs, int n) {
+  constexpr int kVec = 16 / (int)sizeof(Tin);
+  if (m % kVec) return false;
+  for (int i = 0; i < n; ++i)
+    if ((uintptr_t)ptrs[i] % 16) return false;
+  return true;
+}
+
+template <class K>
+static cudaError_t set_smem(K kernel, size_t smem, bool& done) {
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
 template <class Ar, class Tin, class Tred, int R>
 static cudaError_t launch_stage1(const Level& lv, const Tin* a, const Tin* b, const Tin* c,
                                  const Tin* d, Tred* ra, Tred* rb, Tred* rc, Tred* rd, Tred* cg,
                                  Tred* cy, Tred* cv, int* status, cudaStream_t s) {
   constexpr int W = kWarpsPerCta;
-  const size_t smem = WarpTile<Tin, R>::kBytesPerWarp * W;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_stage1<Ar, Tin, Tred, R, W>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  const size_t smem = Tile<Tin, R>::kBytesPerWarp * W;
   const int64_t warps = (lv.k_end - lv.k_begin + 31) / 32;
   const unsigned grid = (unsigned)((warps + W - 1) / W);
   if (grid == 0) return cudaSuccess;
-  k_stage1<Ar, Tin, Tred, R, W><<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, ra, rb, rc, rd, cg, cy,
-                                                           cv, status);
+  const void* ptrs[4] = {a, b, c, d};
+  cudaError_t e;
+  if (vec16_ok<Tin>(lv.m, ptrs, 4)) {
+    static bool done = false;
+    auto k = k_stage1<Ar, Tin, Tred, R, W, true>;
+    if ((e = set_smem(k, smem, done)) != cudaSuccess) return e;
+    k<<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, ra, rb, rc, rd, cg, cy, cv, status);
+  } else {
+    static bool done = false;
+    auto k = k_stage1<Ar, Tin, Tred, R, W, false>;
+    if ((e = set_smem(k, smem, done)) != cudaSuccess) return e;
+    k<<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, ra, rb, rc, rd, cg, cy, cv, status);
+  }
   return cudaGetLastError();
 }
 
@@ -89,19 +114,23 @@ static cudaError_t launch_stage3(const Level& lv, const Tin* a, const Tin* b, co
                                  const Tin* d, const Tred* xr, const Tred* cg, const Tred* cy,
                                  const Tred* cv, Tin* x, int* status, cudaStream_t s) {
   constexpr int W = kWarpsPerCta;
-  const size_t smem = WarpTile<Tin, R>::kBytesPerWarp * W;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_stage3<Ar, Tin, Tred, R, W>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  const size_t smem = Tile<Tin, R>::kBytesPerWarp * W;
   const int64_t warps = (lv.k_end - lv.k_begin + 31) / 32;
   const unsigned grid = (unsigned)((warps + W - 1) / W);
   if (grid == 0) return cudaSuccess;
-  k_stage3<Ar, Tin, Tred, R, W><<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, xr, cg, cy, cv, x,
-                                                           status);
+  const void* ptrs[5] = {a, b, c, d, x};
+  cudaError_t e;
+  if (vec16_ok<Tin>(lv.m, ptrs, 5)) {
+    static bool done = false;
+    auto k = k_stage3<Ar, Tin, Tred, R, W, true>;
+    if ((e = set_smem(k, smem, done)) != cudaSuccess) return e;
+    k<<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, xr, cg, cy, cv, x, status);
+  } else {
+    static bool done = false;
+    auto k = k_stage3<Ar, Tin, Tred, R, W, false>;
+    if ((e = set_smem(k, smem, done)) != cudaSuccess) return e;
+    k<<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, xr, cg, cy, cv, x, status);
+  }
   return cudaGetLastError();
 }
 

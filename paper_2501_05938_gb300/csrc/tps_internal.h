@@ -17,7 +17,7 @@ inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 // Rows per shared-memory chunk (and checkpoint spacing) for an element size.
 inline int chunk_rows(size_t elem_bytes) { return elem_bytes >= 8 ? 8 : 16; }
-constexpr int kWarpsPerCta = 4;
+constexpr int kWarpsPerCta = 1;
 
 // One level of the recursive solve: the system at this level has lv.n rows
 // and is split into lv.p blocks; its reduced system (2 lv.p rows) and the
