@@ -33,6 +33,7 @@ struct ArF64 {
   __device__ __forceinline__ static T mul_nn(T x, T y) { return x * y; }
   // x - y*z, one rounding
   __device__ __forceinline__ static T sub_mul(T x, T y, T z) { return fma(-y, z, x); }
+  __device__ __forceinline__ static T sub_mul_dom(T x, T y, T z) { return fma(-y, z, x); }
   __device__ __forceinline__ static T neg(T x) { return -x; }
   // Newton-Raphson iteration for r = 1/x (r <- r + r(1 - x r)), seeded by
   // the hardware approximation rcp.approx.ftz.f64 and applied twice; each
@@ -60,6 +61,7 @@ struct ArF32 {
   __device__ __forceinline__ static T mul(T x, T y) { return __fmul_rn(x, y); }
   __device__ __forceinline__ static T mul_nn(T x, T y) { return __fmul_rn(x, y); }
   __device__ __forceinline__ static T sub_mul(T x, T y, T z) { return fmaf(-y, z, x); }
+  __device__ __forceinline__ static T sub_mul_dom(T x, T y, T z) { return fmaf(-y, z, x); }
   __device__ __forceinline__ static T neg(T x) { return -x; }
   // hardware reciprocal approximation refined by one Newton-Raphson step
   __device__ __forceinline__ static T rcp(T x) {
@@ -91,17 +93,19 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& 
 
 // Split an fp64 value into hi + lo with integer operations.  hi keeps the
 // sign, the exponent and the leading 24 significand bits (truncated); lo is
-// the remaining 29 bits rounded to 23, built on a power-of-two "magic"
-// float of hi's scale and recovered by one exact fp32 subtraction.
+// the next 23 of the remaining 29 bits (truncated; relative error of the
+// pair < 2^-46), built on a power-of-two "magic" float of hi's scale and
+// recovered by one exact fp32 subtraction.  Values below 2^-103 in
+// magnitude (zero included) give 0; magnitudes from 2^128 up are outside
+// the representable range.
 __device__ __forceinline__ df64 df_split(double v) {
   const unsigned wl = (unsigned)__double2loint(v);
   const unsigned wh = (unsigned)__double2hiint(v);
-  const unsigned ex = (wh >> 20) & 0x7FFu;
-  // exponent 920 .. 1150 <=> float exponent field 24 .. 254
-  const bool ok = (ex - 920u) <= 230u;
+  // biased exponent >= 920 <=> float exponent field >= 24
+  const bool ok = (wh & 0x7FF00000u) >= (920u << 20);
   const unsigned hb = (__funnelshift_l(wl, wh, 3) + 0x40000000u) | (wh & 0x80000000u);
-  const unsigned mag = (hb & 0xFF800000u) - 0x0B800000u;     // +-2^(e-23) of hi
-  const unsigned lob = mag + (((wl & 0x1FFFFFFFu) + 32u) >> 6);
+  const unsigned mag = (hb & 0xFF800000u) - 0x0B800000u;  // +-2^(e-23) of hi
+  const unsigned lob = mag | ((wl >> 6) & 0x007FFFFFu);
   df64 r;
   r.hi = ok ? __uint_as_float(hb) : 0.0f;
   r.lo = ok ? __fsub_rn(__uint_as_float(lob), __uint_as_float(mag)) : 0.0f;
@@ -152,6 +156,20 @@ struct ArDF {
     pe = fmaf(y.lo, z.hi, pe);
     float s, se;
     two_sum(x.hi, -p, s, se);
+    se = __fadd_rn(se, __fsub_rn(x.lo, pe));
+    T r;
+    fast_two_sum(s, se, r.hi, r.lo);
+    return r;
+  }
+  // x - y*z when |x| >= |y*z| is known (the pivot update of a strictly
+  // diagonally dominant matrix): Fast2Sum replaces TwoSum for the high parts.
+  __device__ __forceinline__ static T sub_mul_dom(T x, T y, T z) {
+    const float p = __fmul_rn(y.hi, z.hi);
+    float pe = fmaf(y.hi, z.hi, -p);
+    pe = fmaf(y.hi, z.lo, pe);
+    pe = fmaf(y.lo, z.hi, pe);
+    float s, se;
+    fast_two_sum(x.hi, -p, s, se);
     se = __fadd_rn(se, __fsub_rn(x.lo, pe));
     T r;
     fast_two_sum(s, se, r.hi, r.lo);

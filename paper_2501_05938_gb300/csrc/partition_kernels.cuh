@@ -102,6 +102,14 @@ struct Tile {
   static constexpr size_t kBytesPerWarp = sizeof(Tin) * 2 * kBuf;
 };
 
+// Stage 3 also prefetches each chunk's checkpoint (three values per block)
+// with the chunk: per buffer, 3 x 32 values after the warp's two buffers.
+template <class Tin, class Tred, int R>
+struct Tile3 : Tile<Tin, R> {
+  static constexpr size_t kCkBytesPerBuf = 3 * 32 * sizeof(Tred);
+  static constexpr size_t kBytesPerWarp = Tile<Tin, R>::kBytesPerWarp + 2 * kCkBytesPerBuf;
+};
+
 // 16 bytes of consecutive rows (one 128-bit shared access).
 template <class Tin>
 struct Vec16 {
@@ -196,7 +204,9 @@ __device__ __forceinline__ int warp_lmin(const Level& lv, int64_t k0, int nb) {
 }
 
 // ------------------------------------------------------------------ Stage 1
-template <class Ar, class Tin, class Tred, int R, int W, bool kVec16>
+// R rows per chunk; a checkpoint every K rows (K a multiple of R, and the
+// chunk length of Stage 3).
+template <class Ar, class Tin, class Tred, int R, int K, int W, bool kVec16>
 __global__ void __launch_bounds__(W * 32)
     k_stage1(Level lv, const Tin* __restrict__ a, const Tin* __restrict__ b,
              const Tin* __restrict__ c, const Tin* __restrict__ d, Tred* __restrict__ ra,
@@ -236,7 +246,7 @@ __global__ void __launch_bounds__(W * 32)
   // one interior row (1 <= row <= L-2)
   auto interior = [&](const T av, const T bv, const T cv, const T dv) {
     const T ratio = Ar::mul_nn(av, rbp);
-    beta = Ar::sub_mul(bv, ratio, cprev);
+    beta = Ar::sub_mul_dom(bv, ratio, cprev);
     g = Ar::sub_mul(dv, ratio, g);
     al = Ar::neg(Ar::mul(ratio, al));
     bad |= Ar::bad_pivot(beta);
@@ -267,7 +277,7 @@ __global__ void __launch_bounds__(W * 32)
           interior(Ar::from(xa.v[v]), Ar::from(xb.v[v]), Ar::from(xc.v[v]), Ar::from(xd.v[v]));
       }
     } else {
-#pragma unroll
+#pragma unroll 1
       for (int r = 0; r < R; ++r) {
         const int row = row0 + r;
         if (row < L) {
@@ -279,7 +289,7 @@ __global__ void __launch_bounds__(W * 32)
             interior(av, bv, cv, dv);
           } else {
             const T ratio = Ar::mul_nn(av, rbp);
-            beta = Ar::sub_mul(bv, ratio, cprev);
+            beta = Ar::sub_mul_dom(bv, ratio, cprev);
             g = Ar::sub_mul(dv, ratio, g);
             al = Ar::neg(Ar::mul(ratio, al));
             clast = cv;
@@ -287,9 +297,10 @@ __global__ void __launch_bounds__(W * 32)
         }
       }
     }
-    // checkpoint after the chunk's last row, when the next chunk has interior rows
-    if (active && row0 + R <= L - 2) {
-      const int64_t slot = (int64_t)ch * lv.p + k;
+    // checkpoint after every K rows, when the next K rows start with an
+    // interior row (Stage 3 restarts its K-row chunk there)
+    if (active && ((row0 + R) % K) == 0 && row0 + R <= L - 2) {
+      const int64_t slot = (int64_t)((row0 + R) / K - 1) * lv.p + k;
       Ar::to(ck_gam[slot], Ar::mul(cprev, rbp));
       Ar::to(ck_y[slot], Ar::mul(g, rbp));
       Ar::to(ck_v[slot], Ar::mul(al, rbp));
@@ -321,7 +332,10 @@ __global__ void __launch_bounds__(W * 32)
              const Tred* __restrict__ ck_v, Tin* __restrict__ x, int* __restrict__ status) {
   using T = typename Ar::T;
   using TL = Tile<Tin, R>;
+  using TL3 = Tile3<Tin, Tred, R>;
   constexpr int V = TL::kVec;
+  static_assert(sizeof(T) == sizeof(Tin), "boundary chunks park T values in Tin slots");
+  static_assert(sizeof(Tred) == 4 || sizeof(Tred) == 8, "checkpoint element size");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t k0 = lv.k_begin + ((int64_t)blockIdx.x * W + warp) * 32;
@@ -333,11 +347,23 @@ __global__ void __launch_bounds__(W * 32)
   const int nch = warp_chunks(lv, k0, nb, R);
   const int lmin = warp_lmin(lv, k0, nb);
 
-  Tin* tile = reinterpret_cast<Tin*>(smem_raw) + warp * 2 * TL::kBuf;
+  unsigned char* wbase = smem_raw + warp * TL3::kBytesPerWarp;
+  Tin* tile = reinterpret_cast<Tin*>(wbase);
+  Tred* ckbuf = reinterpret_cast<Tred*>(wbase + TL::kBytesPerWarp);  // [buf][3][32]
   const Tin* const srcs[4] = {a, b, c, d};
   PieceMap<Tin, R> pm;
   pm.init(lv, k0, nb, lane);
+  // the lane's checkpoint for chunk ch (written by Stage 1 after row ch*R-1)
+  auto load_ck = [&](Tred* dst, int ch) {
+    if (active && ch > 0 && ch * R <= L - 2) {
+      const int64_t slot = (int64_t)(ch - 1) * lv.p + k;
+      cp_async<sizeof(Tred)>(dst + lane, ck_gam + slot);
+      cp_async<sizeof(Tred)>(dst + 32 + lane, ck_y + slot);
+      cp_async<sizeof(Tred)>(dst + 64 + lane, ck_v + slot);
+    }
+  };
   load_chunk<Tin, R, kVec16>(tile, srcs, 4, pm, (nch - 1) * R);
+  load_ck(ckbuf, nch - 1);
   cp_async_commit();
 
   T f = Ar::zero(), l = Ar::zero();
@@ -352,7 +378,10 @@ __global__ void __launch_bounds__(W * 32)
   for (int it = 0; it < nch; ++it) {
     const int ch = nch - 1 - it;
     const int row0 = ch * R;
-    if (ch > 0) load_chunk<Tin, R, kVec16>(tile + ((it + 1) & 1) * TL::kBuf, srcs, 4, pm, row0 - R);
+    if (ch > 0) {
+      load_chunk<Tin, R, kVec16>(tile + ((it + 1) & 1) * TL::kBuf, srcs, 4, pm, row0 - R);
+      load_ck(ckbuf + ((it + 1) & 1) * 96, ch - 1);
+    }
     cp_async_commit();
     cp_async_wait<1>();
     __syncwarp();
@@ -362,14 +391,14 @@ __global__ void __launch_bounds__(W * 32)
     // relation entering the chunk: x_{row0-1} = zp - gp * x_{row0}
     T zp = f, gp = Ar::zero();
     if (active && ch > 0 && row0 <= L - 2) {
-      const int64_t slot = (int64_t)(ch - 1) * lv.p + k;
-      gp = Ar::from(ck_gam[slot]);
-      zp = Ar::sub_mul(Ar::from(ck_y[slot]), Ar::from(ck_v[slot]), f);
+      const Tred* ck = ckbuf + (it & 1) * 96;
+      gp = Ar::from(ck[lane]);
+      zp = Ar::sub_mul(Ar::from(ck[32 + lane]), Ar::from(ck[64 + lane]), f);
     }
-    T Z[R], G[R];
-    Tin xo[R];
     const bool fast = ch >= 1 && row0 + R <= lmin - 1;
     if (fast) {
+      T Z[R], G[R];
+      Tin xo[R];
 #pragma unroll
       for (int r = 0; r < R; r += V) {
         const Vec16<Tin> xa = lds16(t + r), xb = lds16(t + TL::kArr + r),
@@ -377,7 +406,7 @@ __global__ void __launch_bounds__(W * 32)
 #pragma unroll
         for (int v = 0; v < V; ++v) {
           const T av = Ar::from(xa.v[v]);
-          const T beta = Ar::sub_mul(Ar::from(xb.v[v]), av, gp);
+          const T beta = Ar::sub_mul_dom(Ar::from(xb.v[v]), av, gp);
           bad |= Ar::bad_pivot(beta);
           const T rbeta = Ar::rcp(beta);
           zp = Ar::mul_nn(Ar::sub_mul(Ar::from(xd.v[v]), av, zp), rbeta);
@@ -391,48 +420,50 @@ __global__ void __launch_bounds__(W * 32)
         xnext = Ar::sub_mul(Z[r], G[r], xnext);
         Ar::to(xo[r], xnext);
       }
-    } else {
 #pragma unroll
+      for (int r = 0; r < R; r += V) {
+        Vec16<Tin> w;
+#pragma unroll
+        for (int v = 0; v < V; ++v) w.v[v] = xo[r + v];
+        *reinterpret_cast<float4*>(t + r) = *reinterpret_cast<const float4*>(&w);
+      }
+    } else {
+      // boundary chunk: the same recurrences, row by row, with the pivots and
+      // right-hand sides parked in the lane's b and c slots
+      T* zs = reinterpret_cast<T*>(t + TL::kArr);
+      T* gs = reinterpret_cast<T*>(t + 2 * TL::kArr);
+#pragma unroll 1
       for (int r = 0; r < R; ++r) {
         const int row = row0 + r;
-        Z[r] = Ar::zero();
-        G[r] = Ar::zero();
         if (row >= 1 && row <= L - 2) {
           const T av = Ar::from(t[r]);
-          const T beta = Ar::sub_mul(Ar::from(t[TL::kArr + r]), av, gp);
+          const T beta = Ar::sub_mul_dom(Ar::from(t[TL::kArr + r]), av, gp);
           bad |= Ar::bad_pivot(beta);
           const T rbeta = Ar::rcp(beta);
           zp = Ar::mul_nn(Ar::sub_mul(Ar::from(t[3 * TL::kArr + r]), av, zp), rbeta);
           gp = Ar::mul_nn(Ar::from(t[2 * TL::kArr + r]), rbeta);
-          Z[r] = zp;
-          G[r] = gp;
+          zs[r] = zp;
+          gs[r] = gp;
         }
       }
-#pragma unroll
+#pragma unroll 1
       for (int r = R - 1; r >= 0; --r) {
         const int row = row0 + r;
-        T xr = Ar::zero();
         if (row < L) {
+          T xr;
           if (row == L - 1) {
             xr = l;
           } else if (row == 0) {
             xr = f;
           } else {
-            xr = Ar::sub_mul(Z[r], G[r], xnext);
+            xr = Ar::sub_mul(zs[r], gs[r], xnext);
             xnext = xr;
           }
+          Ar::to(t[r], xr);
         }
-        Ar::to(xo[r], xr);
       }
     }
-    // x of the chunk into the lane's a slot (no longer needed), then out
-#pragma unroll
-    for (int r = 0; r < R; r += V) {
-      Vec16<Tin> w;
-#pragma unroll
-      for (int v = 0; v < V; ++v) w.v[v] = xo[r + v];
-      *reinterpret_cast<float4*>(t + r) = *reinterpret_cast<const float4*>(&w);
-    }
+    // the chunk's x is in the lanes' a slots (a is no longer needed): out
     __syncwarp();
     store_chunk<Tin, R, kVec16>(x, tb, pm, row0);
     __syncwarp();  // the buffer is refilled by the next iteration's copies

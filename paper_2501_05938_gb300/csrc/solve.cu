@@ -84,11 +84,14 @@ static cudaError_t set_smem(K kernel, size_t smem, bool& done) {
   return e;
 }
 
-template <class Ar, class Tin, class Tred, int R>
+// Stage 1 streams half-size chunks (more warps fit in shared memory) and
+// writes a checkpoint every K rows, K being Stage 3's chunk length.
+template <class Ar, class Tin, class Tred, int K>
 static cudaError_t launch_stage1(const Level& lv, const Tin* a, const Tin* b, const Tin* c,
                                  const Tin* d, Tred* ra, Tred* rb, Tred* rc, Tred* rd, Tred* cg,
                                  Tred* cy, Tred* cv, int* status, cudaStream_t s) {
   constexpr int W = kWarpsPerCta;
+  constexpr int R = K / 2;
   const size_t smem = Tile<Tin, R>::kBytesPerWarp * W;
   const int64_t warps = (lv.k_end - lv.k_begin + 31) / 32;
   const unsigned grid = (unsigned)((warps + W - 1) / W);
@@ -97,12 +100,12 @@ static cudaError_t launch_stage1(const Level& lv, const Tin* a, const Tin* b, co
   cudaError_t e;
   if (vec16_ok<Tin>(lv.m, ptrs, 4)) {
     static bool done = false;
-    auto k = k_stage1<Ar, Tin, Tred, R, W, true>;
+    auto k = k_stage1<Ar, Tin, Tred, R, K, W, true>;
     if ((e = set_smem(k, smem, done)) != cudaSuccess) return e;
     k<<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, ra, rb, rc, rd, cg, cy, cv, status);
   } else {
     static bool done = false;
-    auto k = k_stage1<Ar, Tin, Tred, R, W, false>;
+    auto k = k_stage1<Ar, Tin, Tred, R, K, W, false>;
     if ((e = set_smem(k, smem, done)) != cudaSuccess) return e;
     k<<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, ra, rb, rc, rd, cg, cy, cv, status);
   }
@@ -114,7 +117,7 @@ static cudaError_t launch_stage3(const Level& lv, const Tin* a, const Tin* b, co
                                  const Tin* d, const Tred* xr, const Tred* cg, const Tred* cy,
                                  const Tred* cv, Tin* x, int* status, cudaStream_t s) {
   constexpr int W = kWarpsPerCta;
-  const size_t smem = Tile<Tin, R>::kBytesPerWarp * W;
+  const size_t smem = Tile3<Tin, Tred, R>::kBytesPerWarp * W;
   const int64_t warps = (lv.k_end - lv.k_begin + 31) / 32;
   const unsigned grid = (unsigned)((warps + W - 1) / W);
   if (grid == 0) return cudaSuccess;

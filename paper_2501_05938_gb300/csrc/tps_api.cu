@@ -39,12 +39,12 @@ static cudaEvent_t* next_trace(tps_plan_s* P) {
 }
 
 // Defaults when the caller leaves a parameter at 0 and no predictor is asked
-// for.  Block size 256 keeps the reduced system at n/128 rows (measured best
-// or within 2% of best for n >= 2^24 on GB300); a small system keeps at
+// for.  Block size 128 keeps the reduced system at n/64 rows (measured best,
+// within 1% of m = 256, at n = 2^27 on GB300); a small system keeps at
 // least ~4 blocks per SM so the per-lane serial sweeps run in parallel.
 static void default_params(const tps_plan_desc& d, int32_t& m, int32_t& mr, int32_t& S) {
   if (m == 0) {
-    m = 256;
+    m = 128;
     while (m > 8 && d.n_max / m < 152 * 32 * 4) m /= 2;
   }
   if (mr == 0) mr = 32;
