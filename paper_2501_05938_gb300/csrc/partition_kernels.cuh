@@ -53,6 +53,8 @@ struct Level {
   int64_t p;        // blocks
   int64_t k_begin;  // blocks this launch processes: [k_begin, k_end)
   int64_t k_end;
+  const int64_t* bnd;  // batched systems: first rows of systems 1.., sorted (device)
+  int64_t nbnd;        // number of such rows (0: one system)
   int32_t m;        // nominal block length
   int32_t llast;    // length of block p-1, in [2, m+1]
   int32_t ncap;     // checkpoint slots per block
@@ -62,6 +64,49 @@ struct Level {
 __device__ __forceinline__ int block_len(const Level& lv, int64_t k) {
   return k == lv.p - 1 ? lv.llast : lv.m;
 }
+
+// Systems packed back to back are solved as one system whose couplings are
+// cut at every system boundary: a of a system's first row and c of its last
+// row are taken as 0 (they are never read).  A block may straddle
+// boundaries; its recurrences then decouple exactly there.  Each lane keeps
+// the boundaries that touch its block, bnd[first .. first+cnt).
+struct Bounds {
+  const int64_t* bnd;
+  int64_t first;
+  int cnt;
+  // first index i with bnd[i] >= v
+  __device__ __forceinline__ static int64_t lower(const int64_t* b, int64_t nb, int64_t v) {
+    int64_t lo = 0, hi = nb;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (b[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+  }
+  // boundaries o with start <= o <= start + len (a start row, or the row
+  // after the block's last row)
+  __device__ __forceinline__ void init(const Level& lv, int64_t start, int len, bool active) {
+    bnd = lv.bnd;
+    first = 0;
+    cnt = 0;
+    if (lv.nbnd == 0 || !active) return;
+    first = lower(lv.bnd, lv.nbnd, start);
+    cnt = (int)(lower(lv.bnd, lv.nbnd, start + len + 1) - first);
+  }
+  // a boundary within rows [g0, g0 + rows] (the chunk, or its successor row)
+  __device__ __forceinline__ bool touches(int64_t g0, int rows) const {
+    for (int j = 0; j < cnt; ++j) {
+      const int64_t o = bnd[first + j];
+      if (o >= g0 && o <= g0 + rows) return true;
+    }
+    return false;
+  }
+  __device__ __forceinline__ bool is(int64_t row) const {
+    for (int j = 0; j < cnt; ++j)
+      if (bnd[first + j] == row) return true;
+    return false;
+  }
+};
 
 // Status bits written into the device status word.
 enum : int { ST_BAD_PIVOT = 1, ST_NO_CONVERGENCE = 2, ST_TIMEOUT = 4 };
@@ -233,6 +278,9 @@ __global__ void __launch_bounds__(W * 32)
   pm.init(lv, k0, nb, lane);
   load_chunk<Tin, R, kVec16>(tile, srcs, 4, pm, 0);
   cp_async_commit();
+  const int64_t start = k * (int64_t)lv.m;
+  Bounds bd;
+  bd.init(lv, start, L, active);
 
   // virtual state before row 1 (relation x_0 = f): rbeta = 1, c_prev = 0,
   // g = 0, alpha = -1; first interior unknown x_1 = P - Q f - S x_1 with
@@ -266,7 +314,8 @@ __global__ void __launch_bounds__(W * 32)
     cp_async_wait<1>();
     __syncwarp();
     const Tin* t = tile + (ch & 1) * TL::kBuf + lane * TL::kStride;
-    const bool fast = ch >= 1 && row0 + R <= lmin - 1;
+    const bool fast = ch >= 1 && row0 + R <= lmin - 1 &&
+                      !__any_sync(0xffffffffu, bd.cnt > 0 && bd.touches(start + row0, R));
     if (fast) {
 #pragma unroll
       for (int r = 0; r < R; r += V) {
@@ -281,8 +330,12 @@ __global__ void __launch_bounds__(W * 32)
       for (int r = 0; r < R; ++r) {
         const int row = row0 + r;
         if (row < L) {
-          const T av = Ar::from(t[r]), bv = Ar::from(t[TL::kArr + r]);
-          const T cv = Ar::from(t[2 * TL::kArr + r]), dv = Ar::from(t[3 * TL::kArr + r]);
+          T av = Ar::from(t[r]), cv = Ar::from(t[2 * TL::kArr + r]);
+          const T bv = Ar::from(t[TL::kArr + r]), dv = Ar::from(t[3 * TL::kArr + r]);
+          if (bd.cnt > 0) {  // couplings cut at system boundaries
+            if (bd.is(start + row)) av = Ar::zero();
+            if (bd.is(start + row + 1)) cv = Ar::zero();
+          }
           if (row == 0) {
             a0 = av; b0 = bv; c0 = cv; d0 = dv;
           } else if (row < L - 1) {
@@ -309,16 +362,29 @@ __global__ void __launch_bounds__(W * 32)
   }
   if (active) {
     bad |= Ar::bad_pivot(beta);
-    // first equation of block k, unknowns (l_{k-1}, f_k, l_k)
-    Ar::to(ra[2 * k], k == 0 ? Ar::zero() : a0);
-    Ar::to(rb[2 * k], Ar::sub_mul(b0, c0, Q));
-    Ar::to(rc[2 * k], Ar::neg(Ar::mul(c0, S)));
-    Ar::to(rd[2 * k], Ar::sub_mul(d0, c0, P));
-    // last equation of block k, unknowns (f_k, l_k, f_{k+1})
-    Ar::to(ra[2 * k + 1], al);
-    Ar::to(rb[2 * k + 1], beta);
-    Ar::to(rc[2 * k + 1], k == lv.p - 1 ? Ar::zero() : clast);
-    Ar::to(rd[2 * k + 1], g);
+    if (L == 1) {
+      // a one-row block is a one-row system (tails are merged otherwise):
+      // b0 f = d0, and a decoupled identity row for the unused l
+      Ar::to(ra[2 * k], Ar::zero());
+      Ar::to(rb[2 * k], b0);
+      Ar::to(rc[2 * k], Ar::zero());
+      Ar::to(rd[2 * k], d0);
+      Ar::to(ra[2 * k + 1], Ar::zero());
+      Ar::to(rb[2 * k + 1], Ar::one());
+      Ar::to(rc[2 * k + 1], Ar::zero());
+      Ar::to(rd[2 * k + 1], Ar::zero());
+    } else {
+      // first equation of block k, unknowns (l_{k-1}, f_k, l_k)
+      Ar::to(ra[2 * k], k == 0 ? Ar::zero() : a0);
+      Ar::to(rb[2 * k], Ar::sub_mul(b0, c0, Q));
+      Ar::to(rc[2 * k], Ar::neg(Ar::mul(c0, S)));
+      Ar::to(rd[2 * k], Ar::sub_mul(d0, c0, P));
+      // last equation of block k, unknowns (f_k, l_k, f_{k+1})
+      Ar::to(ra[2 * k + 1], al);
+      Ar::to(rb[2 * k + 1], beta);
+      Ar::to(rc[2 * k + 1], k == lv.p - 1 ? Ar::zero() : clast);
+      Ar::to(rd[2 * k + 1], g);
+    }
     if (bad) atomicOr(status, ST_BAD_PIVOT);
   }
 }
@@ -366,6 +432,9 @@ __global__ void __launch_bounds__(W * 32)
   load_ck(ckbuf, nch - 1);
   cp_async_commit();
 
+  const int64_t start = k * (int64_t)lv.m;
+  Bounds bd;
+  bd.init(lv, start, L, active);
   T f = Ar::zero(), l = Ar::zero();
   if (active) {
     f = Ar::from(xred[2 * k]);
@@ -395,7 +464,8 @@ __global__ void __launch_bounds__(W * 32)
       gp = Ar::from(ck[lane]);
       zp = Ar::sub_mul(Ar::from(ck[32 + lane]), Ar::from(ck[64 + lane]), f);
     }
-    const bool fast = ch >= 1 && row0 + R <= lmin - 1;
+    const bool fast = ch >= 1 && row0 + R <= lmin - 1 &&
+                      !__any_sync(0xffffffffu, bd.cnt > 0 && bd.touches(start + row0, R));
     if (fast) {
       T Z[R], G[R];
       Tin xo[R];
@@ -436,12 +506,16 @@ __global__ void __launch_bounds__(W * 32)
       for (int r = 0; r < R; ++r) {
         const int row = row0 + r;
         if (row >= 1 && row <= L - 2) {
-          const T av = Ar::from(t[r]);
+          T av = Ar::from(t[r]), cv = Ar::from(t[2 * TL::kArr + r]);
+          if (bd.cnt > 0) {  // couplings cut at system boundaries
+            if (bd.is(start + row)) av = Ar::zero();
+            if (bd.is(start + row + 1)) cv = Ar::zero();
+          }
           const T beta = Ar::sub_mul_dom(Ar::from(t[TL::kArr + r]), av, gp);
           bad |= Ar::bad_pivot(beta);
           const T rbeta = Ar::rcp(beta);
           zp = Ar::mul_nn(Ar::sub_mul(Ar::from(t[3 * TL::kArr + r]), av, zp), rbeta);
-          gp = Ar::mul_nn(Ar::from(t[2 * TL::kArr + r]), rbeta);
+          gp = Ar::mul_nn(cv, rbeta);
           zs[r] = zp;
           gs[r] = gp;
         }
@@ -451,10 +525,10 @@ __global__ void __launch_bounds__(W * 32)
         const int row = row0 + r;
         if (row < L) {
           T xr;
-          if (row == L - 1) {
-            xr = l;
-          } else if (row == 0) {
+          if (row == 0) {
             xr = f;
+          } else if (row == L - 1) {
+            xr = l;
           } else {
             xr = Ar::sub_mul(zs[r], gs[r], xnext);
             xnext = xr;
@@ -482,7 +556,7 @@ template <class Ar, class Tin, class Tout>
 __global__ void __launch_bounds__(32)
     k_base(int64_t n, const Tin* __restrict__ a, const Tin* __restrict__ b,
            const Tin* __restrict__ c, const Tin* __restrict__ d, Tout* __restrict__ x,
-           int* __restrict__ status) {
+           const int64_t* __restrict__ bnd, int64_t nbnd, int* __restrict__ status) {
   using T = typename Ar::T;
   __shared__ T sa[kBaseMax], sb[kBaseMax], sc[kBaseMax], sd[kBaseMax];
   const int lane = threadIdx.x;
@@ -491,9 +565,14 @@ __global__ void __launch_bounds__(32)
   for (int h = 0; h < 2; ++h) {
     const int i = lane + 32 * h;
     if (i < nn) {
-      sa[i] = (i == 0) ? Ar::zero() : Ar::from(a[i]);
+      bool start = (i == 0), end = (i == nn - 1);
+      for (int64_t j = 0; j < nbnd; ++j) {  // packed systems: cut the couplings
+        start |= bnd[j] == i;
+        end |= bnd[j] == i + 1;
+      }
+      sa[i] = start ? Ar::zero() : Ar::from(a[i]);
       sb[i] = Ar::from(b[i]);
-      sc[i] = (i == nn - 1) ? Ar::zero() : Ar::from(c[i]);
+      sc[i] = end ? Ar::zero() : Ar::from(c[i]);
       sd[i] = Ar::from(d[i]);
     } else {
       sa[i] = Ar::zero(); sb[i] = Ar::one(); sc[i] = Ar::zero(); sd[i] = Ar::zero();

@@ -23,6 +23,8 @@ Level make_level(int64_t n, int m, int R) {
   lv.p = p;
   lv.k_begin = 0;
   lv.k_end = p;
+  lv.bnd = nullptr;
+  lv.nbnd = 0;
   lv.llast = (int32_t)last;
   // checkpoint slots: a block of length L has floor((L - 2) / R) of them;
   // size for the longest block (m + 1) so the count is monotone in n
@@ -143,7 +145,7 @@ static cudaError_t run_levels(tps_plan_s* P, const std::vector<LevelPlan>& level
                               Tin* x, cudaStream_t s) {
   if (idx == levels.size()) {
     if (n <= 0) return cudaSuccess;
-    k_base<Ar, Tin, Tin><<<1, 32, 0, s>>>(n, a, b, c, d, x, P->d_status);
+    k_base<Ar, Tin, Tin><<<1, 32, 0, s>>>(n, a, b, c, d, x, nullptr, 0, P->d_status);
     return cudaGetLastError();
   }
   const LevelPlan& L = levels[idx];
@@ -230,27 +232,29 @@ cudaError_t reduced_solve(tps_plan_s* P, const std::vector<LevelPlan>& levels, c
   });
 }
 
-// The one-warp solve of a system of at most kBaseMax rows.
+// The one-warp solve of a system of at most kBaseMax rows (bnd: first rows
+// of packed systems 1.., or null).
 cudaError_t base_solve(tps_plan_s* P, int64_t n, const void* a, const void* b, const void* c,
-                       const void* d, void* x, cudaStream_t s) {
+                       const void* d, void* x, cudaStream_t s, const int64_t* bnd,
+                       int64_t nbnd) {
   return dispatch(P->desc.dtype, [&](auto ar, auto* tin, auto* tred) -> cudaError_t {
     using Ar = decltype(ar);
     using Tin = std::remove_pointer_t<decltype(tin)>;
     (void)tred;
     k_base<Ar, Tin, Tin><<<1, 32, 0, s>>>(n, (const Tin*)a, (const Tin*)b, (const Tin*)c,
-                                          (const Tin*)d, (Tin*)x, P->d_status);
+                                          (const Tin*)d, (Tin*)x, bnd, nbnd, P->d_status);
     return cudaGetLastError();
   });
 }
 
 tps_status run_solve(tps_plan_s* P, int64_t n, const void* a, const void* b, const void* c,
                      const void* d, void* x, cudaStream_t s, const std::vector<LevelPlan>& lv,
-                     cudaEvent_t* ev) {
+                     cudaEvent_t* ev, const int64_t* bnd, int64_t nbnd) {
   cudaError_t e = cudaSuccess;
   if (ev) e = cudaEventRecord(ev[0], s);
   if (lv.empty()) {
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
-    if (e == cudaSuccess) e = base_solve(P, n, a, b, c, d, x, s);
+    if (e == cudaSuccess) e = base_solve(P, n, a, b, c, d, x, s, bnd, nbnd);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
   } else {
     if (e == cudaSuccess) e = stage1_range(P, lv[0], 0, lv[0].lv.p, a, b, c, d, s);

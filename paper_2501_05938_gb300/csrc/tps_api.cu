@@ -309,9 +309,41 @@ tps_status tps_solve(tps_plan_t P, int64_t n, const void* a, const void* b, cons
 tps_status tps_solve_batched(tps_plan_t P, int64_t count, const int64_t* offsets,
                              const int64_t* host_offsets, const void* a, const void* b,
                              const void* c, const void* d, void* x, void* stream) {
-  (void)P; (void)count; (void)offsets; (void)host_offsets; (void)a; (void)b; (void)c; (void)d;
-  (void)x; (void)stream;
-  return TPS_ERR_UNSUPPORTED;
+  if (!P || count < 0 || (count > 0 && !offsets)) return TPS_ERR_INVALID_ARG;
+  if (P->desc.dtype == TPS_MIXED_F32_F64) return TPS_ERR_UNSUPPORTED;
+  if (count > P->desc.batch_max) return TPS_ERR_INVALID_ARG;
+  if (count == 0) return TPS_OK;
+  if ((uintptr_t)offsets % 8) return TPS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t n = 0;
+  if (host_offsets) {
+    if (host_offsets[0] != 0) return TPS_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < count; ++i)
+      if (host_offsets[i + 1] < host_offsets[i]) return TPS_ERR_INVALID_ARG;
+    n = host_offsets[count];
+  } else {
+    int64_t ends[2];
+    if (cudaMemcpyAsync(ends, offsets + count - 1, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                        s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return TPS_ERR_CUDA;
+    n = ends[1];
+  }
+  tps_status st = check_solve_args(P, n, a, b, c, d, x, false);
+  if (st != TPS_OK || n == 0) return st;
+  P->last_stream = s;
+  std::vector<LevelPlan> lv;
+  build_levels(n, P->m, P->m_reduced, elem_bytes_io(P->desc.dtype),
+               elem_bytes_red(P->desc.dtype), P->off_levels, lv);
+  P->last_levels = (int32_t)lv.size();
+  // system boundaries strictly inside [0, n): offsets[1 .. count-1]
+  const int64_t* bnd = count > 1 ? offsets + 1 : nullptr;
+  const int64_t nbnd = count - 1;
+  if (!lv.empty()) {
+    lv[0].lv.bnd = bnd;
+    lv[0].lv.nbnd = nbnd;
+  }
+  return run_solve(P, n, a, b, c, d, x, s, lv, next_trace(P), bnd, nbnd);
 }
 
 tps_status tps_solve_host_async(tps_plan_t P, int64_t n, const void* a, const void* b,

@@ -77,9 +77,11 @@ namespace tps {
 // dtype selects the arithmetic; a..x are device pointers of the I/O type.
 // ev (optional, 4 events) is recorded before Stage 1, after Stage 1, after
 // Stage 2 and after Stage 3 of level 0.
+// bnd/nbnd: for packed systems, the first rows of systems 1.. (device,
+// sorted); the couplings there are cut.  lv[0].lv must carry the same.
 tps_status run_solve(tps_plan_s* P, int64_t n, const void* a, const void* b, const void* c,
                      const void* d, void* x, cudaStream_t s, const std::vector<LevelPlan>& lv,
-                     cudaEvent_t* ev);
+                     cudaEvent_t* ev, const int64_t* bnd = nullptr, int64_t nbnd = 0);
 
 // Level-0 pieces of the solve for the chunked host pipeline: Stage 1 and
 // Stage 3 on blocks [kb, ke), Stage 2 on the whole reduced system, and the
@@ -92,7 +94,8 @@ cudaError_t stage3_range(tps_plan_s* P, const LevelPlan& L, int64_t kb, int64_t 
                          cudaStream_t s);
 cudaError_t reduced_solve(tps_plan_s* P, const std::vector<LevelPlan>& levels, cudaStream_t s);
 cudaError_t base_solve(tps_plan_s* P, int64_t n, const void* a, const void* b, const void* c,
-                       const void* d, void* x, cudaStream_t s);
+                       const void* d, void* x, cudaStream_t s, const int64_t* bnd = nullptr,
+                       int64_t nbnd = 0);
 
 size_t elem_bytes_io(int dtype);
 size_t elem_bytes_red(int dtype);
