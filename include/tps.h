@@ -152,6 +152,35 @@ tps_status tps_solve_batched(tps_plan_t plan, int64_t count, const int64_t* offs
 tps_status tps_solve_host_async(tps_plan_t plan, int64_t n, const void* a, const void* b,
                                 const void* c, const void* d, void* x, void* stream);
 
+/* Largest system tps_solve_noalloc accepts, in rows. */
+#define TPS_NOALLOC_MAX_ROWS 262144
+
+/* The device-resident solve of tps_solve for callers that cannot allocate
+ * device memory: code inside a framework whose caching allocator must own
+ * every device buffer, code running under a fixed device-memory budget, or
+ * a latency-critical loop where a cudaMalloc (which may synchronise the
+ * device) is not acceptable.  It needs no plan and
+ * allocates nothing: its scratch (reduced systems, Stage-1 checkpoints, a
+ * status word) is one fixed 2 MiB array in device memory that every GPU
+ * loading libtps holds until the process exits.  The paper has no
+ * counterpart to this entry point.
+ *   dtype       TPS_F64, TPS_F64_DF or TPS_F32 (as in tps_plan_desc)
+ *   n           0 .. TPS_NOALLOC_MAX_ROWS; larger n gives TPS_ERR_INVALID_ARG
+ *   a, b, c, d  device inputs, x device output (n elements of the I/O type;
+ *               x must not overlap an input), owned by the caller
+ *   status_out  optional device int32 that receives TPS_OK or
+ *               TPS_ERR_ZERO_PIVOT when the solve has run (NULL: not reported)
+ *   stream      cudaStream_t as void*
+ * Fixed parameters: m = 64 at the top level, 32 below.  The first call on a
+ * device looks up the scratch array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream
+ * capture.  Every call overwrites the shared scratch, so calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller. */
+tps_status tps_solve_noalloc(int32_t dtype, int64_t n, const void* a, const void* b,
+                             const void* c, const void* d, void* x, int32_t* status_out,
+                             void* stream);
+
 /* Report the plan's parameters and the numeric status of the solves since
  * the previous query (synchronises the plan's last stream, reads the device
  * status word and clears it). */
