@@ -72,6 +72,11 @@ struct ArF32 {
   __device__ __forceinline__ static bool bad_pivot(T x) { return !(fabsf(x) >= 1.17549435e-38f); }
   __device__ __forceinline__ static T from(float v) { return v; }
   __device__ __forceinline__ static void to(float& dst, T v) { dst = v; }
+  // fp64 storage (the fp32 elimination of the mixed-precision solve): the
+  // value truncated to binary32 and widened back exactly, both with integer
+  // operations (the conversion instructions run at the slow fp64 rate)
+  __device__ __forceinline__ static T from(double v);
+  __device__ __forceinline__ static void to(double& dst, T v);
 };
 
 // ------------------------------------------------------------------ double-float
@@ -121,6 +126,9 @@ __device__ __forceinline__ double f32_widen_bits(float f) {
   const unsigned wl = u << 29;
   return __hiloint2double((int)wh, (int)wl);
 }
+
+__device__ __forceinline__ float ArF32::from(double v) { return df_split(v).hi; }
+__device__ __forceinline__ void ArF32::to(double& dst, float v) { dst = f32_widen_bits(v); }
 
 struct ArDF {
   using T = df64;

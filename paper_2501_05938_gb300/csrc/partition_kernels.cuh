@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(W * 32)
   using TL = Tile<Tin, R>;
   using TL3 = Tile3<Tin, Tred, R>;
   constexpr int V = TL::kVec;
-  static_assert(sizeof(T) == sizeof(Tin), "boundary chunks park T values in Tin slots");
+  static_assert(sizeof(T) <= sizeof(Tin), "boundary chunks park T values in Tin slots");
   static_assert(sizeof(Tred) == 4 || sizeof(Tred) == 8, "checkpoint element size");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

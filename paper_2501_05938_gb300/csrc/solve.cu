@@ -62,7 +62,9 @@ size_t build_levels(int64_t n, int m0, int mr, size_t top_elem, size_t red_elem,
 }
 
 size_t elem_bytes_io(int dtype) { return dtype == TPS_F32 ? 4 : 8; }
-size_t elem_bytes_red(int dtype) { return dtype == TPS_F32 ? 4 : 8; }
+size_t elem_bytes_red(int dtype) {
+  return (dtype == TPS_F32 || dtype == TPS_MIXED_F32_F64) ? 4 : 8;
+}
 
 // ------------------------------------------------------------------ launchers
 // 16-byte copies need 16-byte aligned arrays and blocks that start on a
@@ -173,6 +175,7 @@ static cudaError_t dispatch(int dtype, F&& f) {
     case TPS_F64: return f(ArF64{}, (double*)nullptr, (double*)nullptr);
     case TPS_F64_DF: return f(ArDF{}, (double*)nullptr, (float2*)nullptr);
     case TPS_F32: return f(ArF32{}, (float*)nullptr, (float*)nullptr);
+    case TPS_MIXED_F32_F64: return f(ArF32{}, (double*)nullptr, (float*)nullptr);
   }
   return cudaErrorInvalidValue;
 }

@@ -54,9 +54,9 @@ static void default_params(const tps_plan_desc& d, int32_t& m, int32_t& mr, int3
 extern "C" int tps_predict_params(const tps_plan_desc* desc, int32_t* m, int32_t* streams,
                                   int64_t* chunk);
 
-static size_t workspace_for(const tps_plan_s* P, size_t* off_levels_out, size_t* off_dev_out) {
+static size_t workspace_for(tps_plan_s* P, size_t* off_levels_out, size_t* off_dev_out) {
   size_t off = 0;
-  off = align_up(off + 64);  // status word and refinement scalars
+  off = align_up(off + 64);  // status word and refinement maxima
   *off_levels_out = off;
   std::vector<LevelPlan> lv;
   const size_t eio = elem_bytes_io(P->desc.dtype);
@@ -64,11 +64,10 @@ static size_t workspace_for(const tps_plan_s* P, size_t* off_levels_out, size_t*
   int64_t nmax = P->desc.n_max;
   size_t end = build_levels(nmax, P->m, P->m_reduced, eio, ered, off, lv);
   if (P->desc.dtype == TPS_MIXED_F32_F64) {
-    // inner fp32 solve levels (reduced storage fp32) + residual and
-    // correction vectors (fp64) -- sized generously with fp64 elements
-    end = build_levels(nmax, P->m, P->m_reduced, 8, 8, off, lv);
-    end = align_up(end + (size_t)nmax * 8);  // r
-    end = align_up(end + (size_t)nmax * 8);  // delta
+    // residual r and correction delta (fp64)
+    P->off_refine = end;
+    end = align_up(end + (size_t)nmax * 8);
+    end = align_up(end + (size_t)nmax * 8);
   }
   off = end;
   *off_dev_out = off;
@@ -298,11 +297,13 @@ tps_status tps_solve(tps_plan_t P, int64_t n, const void* a, const void* b, cons
   if (st != TPS_OK || n == 0) return st;
   cudaStream_t s = (cudaStream_t)stream;
   P->last_stream = s;
-  if (P->desc.dtype == TPS_MIXED_F32_F64) return TPS_ERR_UNSUPPORTED;
   std::vector<LevelPlan> lv;
   build_levels(n, P->m, P->m_reduced, elem_bytes_io(P->desc.dtype),
                elem_bytes_red(P->desc.dtype), P->off_levels, lv);
   P->last_levels = (int32_t)lv.size();
+  if (P->desc.dtype == TPS_MIXED_F32_F64)
+    return run_refine(P, n, (const double*)a, (const double*)b, (const double*)c,
+                      (const double*)d, (double*)x, s, lv, nullptr, 0);
   return run_solve(P, n, a, b, c, d, x, s, lv, next_trace(P));
 }
 
@@ -310,7 +311,6 @@ tps_status tps_solve_batched(tps_plan_t P, int64_t count, const int64_t* offsets
                              const int64_t* host_offsets, const void* a, const void* b,
                              const void* c, const void* d, void* x, void* stream) {
   if (!P || count < 0 || (count > 0 && !offsets)) return TPS_ERR_INVALID_ARG;
-  if (P->desc.dtype == TPS_MIXED_F32_F64) return TPS_ERR_UNSUPPORTED;
   if (count > P->desc.batch_max) return TPS_ERR_INVALID_ARG;
   if (count == 0) return TPS_OK;
   if ((uintptr_t)offsets % 8) return TPS_ERR_INVALID_ARG;
@@ -343,6 +343,9 @@ tps_status tps_solve_batched(tps_plan_t P, int64_t count, const int64_t* offsets
     lv[0].lv.bnd = bnd;
     lv[0].lv.nbnd = nbnd;
   }
+  if (P->desc.dtype == TPS_MIXED_F32_F64)
+    return run_refine(P, n, (const double*)a, (const double*)b, (const double*)c,
+                      (const double*)d, (double*)x, s, lv, bnd, nbnd);
   return run_solve(P, n, a, b, c, d, x, s, lv, next_trace(P), bnd, nbnd);
 }
 

@@ -54,6 +54,7 @@ struct tps_plan_s {
   int* d_status = nullptr;     // device status word (first bytes of ws)
   double* d_scalars = nullptr; // refinement reductions (next bytes of ws)
   size_t off_levels = 0;       // first level buffer offset
+  size_t off_refine = 0;       // refinement residual and correction vectors
   cudaStream_t last_stream = nullptr;
   int32_t last_levels = 0;
   int32_t last_iters = 0;
@@ -96,6 +97,13 @@ cudaError_t reduced_solve(tps_plan_s* P, const std::vector<LevelPlan>& levels, c
 cudaError_t base_solve(tps_plan_s* P, int64_t n, const void* a, const void* b, const void* c,
                        const void* d, void* x, cudaStream_t s, const int64_t* bnd = nullptr,
                        int64_t nbnd = 0);
+
+// Mixed-precision refinement of one device-resident system (or packed
+// systems): fp32 partition elimination, fp64 residual and update.  Reads two
+// maxima back to the host after every correction (synchronises `s`).
+tps_status run_refine(tps_plan_s* P, int64_t n, const double* a, const double* b,
+                      const double* c, const double* d, double* x, cudaStream_t s,
+                      const std::vector<LevelPlan>& lv, const int64_t* bnd, int64_t nbnd);
 
 size_t elem_bytes_io(int dtype);
 size_t elem_bytes_red(int dtype);
