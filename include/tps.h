@@ -181,6 +181,85 @@ tps_status tps_solve_noalloc(int32_t dtype, int64_t n, const void* a, const void
                              const void* c, const void* d, void* x, int32_t* status_out,
                              void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Launch-parameter selection.  The paper fits a model of the optimum stream
+ * count (Sec. 2.4: Eq. 4 and Eq. 7 fed into Eq. 6); this library adds a small
+ * learned predictor, an MLP trained on the GPU on timings the solver itself
+ * produced, that chooses the block size m, the stream count S and the chunk
+ * size from (log2 n, log2 batch, dtype, residency).
+ * ------------------------------------------------------------------------- */
+#define TPS_MLP_IN 4
+#define TPS_MLP_HIDDEN 64
+#define TPS_MLP_OUT 3
+/* [W1 (64x4), b1 (64), W2 (64x64), b2 (64), W3 (3x64), b3 (3)], row-major
+ * [out][in], fp32 */
+#define TPS_MLP_NPARAMS 4675
+
+/* fp32 scratch (in floats) that tps_mlp_forward / tps_mlp_loss_backward need
+ * for a batch of `batch` samples. */
+size_t tps_mlp_workspace_floats(int32_t batch);
+
+/* Y[batch][3] = MLP(X[batch][4]) on the device (two ReLU hidden layers of
+ * 64).  All pointers are device memory owned by the caller; `work` holds
+ * tps_mlp_workspace_floats(batch) floats. */
+tps_status tps_mlp_forward(const float* params, int32_t batch, const float* X, float* Y,
+                           float* work, void* stream);
+
+/* Forward pass, loss L = mean((Y - T)^2) over batch and outputs (written to
+ * *loss, device, may be NULL) and the gradient dL/dparams (grads, device,
+ * TPS_MLP_NPARAMS floats, overwritten). */
+tps_status tps_mlp_loss_backward(const float* params, int32_t batch, const float* X,
+                                 const float* T, float* grads, float* loss, float* work,
+                                 void* stream);
+
+/* One Adam step (Kingma and Ba) on the device: m, v are the moment buffers
+ * (TPS_MLP_NPARAMS floats, zero before step t = 1). */
+tps_status tps_mlp_adam_step(float* params, const float* grads, float* m, float* v, int32_t t,
+                             float lr, float beta1, float beta2, float eps, void* stream);
+
+/* The same forward pass on the host for one sample (x[4] -> y[3]); the
+ * multiply-add order matches the device kernels, so results agree bit for
+ * bit. */
+void tps_mlp_forward_host(const float* params, const float* x, float* y);
+
+/* Fill m, streams and chunk for `desc` from the installed predictor weights
+ * ($TPS_PREDICTOR_WEIGHTS, else predictor/weights.bin beside libtps.so).
+ * Returns 0 on success, 1 when no weights are installed, 2 on bad
+ * arguments.  chunk = 0 means one chunk per stream. */
+int tps_predict_params(const tps_plan_desc* desc, int32_t* m, int32_t* streams,
+                       int64_t* chunk);
+
+/* 1 if predictor weights could be loaded, else 0. */
+int tps_predict_available(void);
+
+/* Load predictor weights from `path` (the training driver's file format),
+ * replacing any loaded ones.  Returns 0 on success, 1 if the file is
+ * missing or malformed, 2 for a NULL path. */
+int tps_predict_load(const char* path);
+
+/* Exhaustive search: time tps_solve (count == 0: one system of n rows) or
+ * tps_solve_batched (count > 0, offsets as there) on the caller's data for
+ * every block size m in {16, 32, ..., 1024} whose workspace fits the plan,
+ * `reps` timed solves each after one warm-up, and keep the fastest m in the
+ * plan.  A plan created with TPS_TUNE_EXHAUSTIVE sizes its workspace for the
+ * whole grid.  Synchronises `stream`; x is overwritten.  *best_m and
+ * *best_ms (may be NULL) receive the choice and its mean time. */
+tps_status tps_autotune(tps_plan_t plan, int64_t n, int64_t count, const int64_t* offsets,
+                        const int64_t* host_offsets, const void* a, const void* b,
+                        const void* c, const void* d, void* x, void* stream, int32_t reps,
+                        int32_t* best_m, float* best_ms);
+
+/* The paper's optimum-stream rule (Sec. 2.4, Eq. 6) with the sum model of
+ * Eq. 4 (sum_model[2]: slope, intercept) and the overhead models of Eq. 7
+ * (small[3]: size, log10 S and constant coefficients, for size <= split;
+ * big[3]: size and constant inside the log2(S^(4/3)) factor, then the
+ * constant, for size > split).  NULL coefficient pointers select the
+ * paper's RTX 2080 Ti values; split <= 0 selects 1e6.  Returns S in
+ * {1, 2, 4, 8, 16, 32}: among S with T_overhead(S) < (S-1)/S * sum the one
+ * with the largest slack, or 1 when none qualifies. */
+int32_t tps_paper_predict_streams(double size, const double* sum_model, const double* small,
+                                  const double* big, double split);
+
 /* Report the plan's parameters and the numeric status of the solves since
  * the previous query (synchronises the plan's last stream, reads the device
  * status word and clears it). */

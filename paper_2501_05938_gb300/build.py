@@ -57,7 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> None:
         objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
         with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
             list(ex.map(lambda so: _compile(*so), zip(srcs, objs)))
-        cmd = [_nvcc(), *ARCH, "-shared", "-o", LIBTPS + ".tmp", *objs, "-lcudart"]
+        cmd = [_nvcc(), *ARCH, "-shared", "-o", LIBTPS + ".tmp", *objs, "-lcudart", "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -30,6 +30,7 @@ static tps_status cuda_status(cudaError_t e) {
 }
 
 constexpr int kTraceSlots = 256;
+constexpr int32_t kTuneMin = 16, kTuneMax = 1024;  // autotuner block-size grid
 
 static cudaEvent_t* next_trace(tps_plan_s* P) {
   if (!P->trace_ev) return nullptr;
@@ -50,9 +51,6 @@ static void default_params(const tps_plan_desc& d, int32_t& m, int32_t& mr, int3
   if (mr == 0) mr = 32;
   if (S == 0) S = (d.residency == TPS_HOST_PINNED) ? 4 : 1;
 }
-
-extern "C" int tps_predict_params(const tps_plan_desc* desc, int32_t* m, int32_t* streams,
-                                  int64_t* chunk);
 
 static size_t workspace_for(tps_plan_s* P, size_t* off_levels_out, size_t* off_dev_out) {
   size_t off = 0;
@@ -133,7 +131,21 @@ tps_status tps_plan(const tps_plan_desc* desc, tps_plan_t* out) {
   default_params(d, P->m, P->m_reduced, P->streams);
 
   size_t off_levels = 0, off_dev = 0;
-  P->ws_needed = workspace_for(P, &off_levels, &off_dev);
+  if (d.flags & TPS_TUNE_EXHAUSTIVE) {
+    // the autotuner's smallest block size needs the largest workspace
+    const int32_t keep = P->m;
+    P->m = kTuneMin;
+    P->ws_needed = workspace_for(P, &off_levels, &off_dev);
+    P->m = keep;
+    size_t o2 = 0, d2 = 0;
+    const size_t own = workspace_for(P, &o2, &d2);
+    if (own > P->ws_needed) {
+      P->ws_needed = own;
+      off_dev = d2;
+    }
+  } else {
+    P->ws_needed = workspace_for(P, &off_levels, &off_dev);
+  }
   P->off_levels = off_levels;
 
   if (d.residency == TPS_HOST_PINNED) {
@@ -432,6 +444,56 @@ tps_status tps_solve_host_async(tps_plan_t P, int64_t n, const void* a, const vo
   }
   P->last_stream = us;
   return e == cudaSuccess ? TPS_OK : TPS_ERR_CUDA;
+}
+
+tps_status tps_autotune(tps_plan_t P, int64_t n, int64_t count, const int64_t* offsets,
+                        const int64_t* host_offsets, const void* a, const void* b,
+                        const void* c, const void* d, void* x, void* stream, int32_t reps,
+                        int32_t* best_m, float* best_ms) {
+  if (!P || reps < 1 || count < 0) return TPS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  auto solve = [&]() -> tps_status {
+    return count == 0 ? tps_solve(P, n, a, b, c, d, x, stream)
+                      : tps_solve_batched(P, count, offsets, host_offsets, a, b, c, d, x,
+                                          stream);
+  };
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return TPS_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return TPS_ERR_CUDA;
+  }
+  const int32_t keep = P->m;
+  int32_t best = keep;
+  float best_t = -1.0f;
+  tps_status st = TPS_OK;
+  for (int32_t m = kTuneMin; m <= kTuneMax && st == TPS_OK; m *= 2) {
+    P->m = m;
+    size_t o1 = 0, o2 = 0;
+    if (workspace_for(P, &o1, &o2) > P->ws_bytes) continue;  // does not fit this plan
+    st = solve();  // warm-up
+    if (st != TPS_OK) break;
+    if (cudaEventRecord(e0, s) != cudaSuccess) { st = TPS_ERR_CUDA; break; }
+    for (int r = 0; r < reps && st == TPS_OK; ++r) st = solve();
+    if (st != TPS_OK) break;
+    float ms = 0.0f;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      st = TPS_ERR_CUDA;
+      break;
+    }
+    ms /= reps;
+    if (best_t < 0.0f || ms < best_t) {
+      best_t = ms;
+      best = m;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  P->m = (st == TPS_OK && best_t >= 0.0f) ? best : keep;
+  if (best_m) *best_m = P->m;
+  if (best_ms) *best_ms = best_t;
+  return st;
 }
 
 tps_status tps_plan_query(tps_plan_t P, tps_info* out) {

@@ -1,0 +1,438 @@
+"""Launch-parameter tuning: timing sweeps, predictor training, regret.
+
+  collect  time the solver on this GPU over the parameter grid: block size m
+           for device-resident single and batched solves, stream count S and
+           chunk size for the host-resident pipeline, fp64 (double-float) and
+           fp32, n = 2^10 .. 2^28 and 3 * 2^k; writes a CSV
+  train    per point the fastest configuration (exhaustive search) is the
+           target; the MLP (4 -> 64 -> 64 -> 3, ReLU) is trained on the
+           GPU with libtps's CUDA kernels (tps_mlp_loss_backward,
+           tps_mlp_adam_step) on the training points; writes weights.bin
+  evaluate regret T(choice)/T(best) - 1 on held-out points (odd exponents,
+           3 * 2^k sizes, an unseen batch count) for the MLP, for the paper's
+           stream rule (Eq. 4, 6, 7) refit on this GPU's timings, and for the
+           fixed defaults
+
+Usage: python -m paper_2501_05938_gb300.tune collect|train|evaluate|all [dir]
+"""
+from __future__ import annotations
+
+import csv
+import ctypes
+import json
+import math
+import os
+import struct
+import sys
+import time
+
+import numpy as np
+
+from . import binding
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+PRED_DIR = os.path.join(HERE, "predictor")
+
+M_GRID = (8, 16, 32, 64, 128, 256, 512, 1024)
+S_GRID = (1, 2, 4, 8, 16, 32)
+CHUNK_GRID = (0, 1 << 18, 1 << 20, 1 << 22, 1 << 24)  # 0: n/S rows per chunk
+M_HOST = 128
+BATCHES = (16, 256, 1024, 4096)
+HELD_OUT_BATCH = 1024
+DTYPES = {"f64_df": 0, "f32": 1}
+FIELDS = ("kind", "n", "batch", "dtype", "residency", "m", "S", "chunk", "ms", "s13_ms")
+
+
+def sizes():
+    out = [1 << k for k in range(10, 29)]
+    out += [3 << k for k in (12, 16, 20, 24)]
+    return sorted(out)
+
+
+def held_out(rec):
+    n, batch = int(rec["n"]), int(rec["batch"])
+    if batch == HELD_OUT_BATCH:
+        return True
+    if batch > 1:
+        return False
+    k = math.log2(n)
+    return (k != int(k)) or (int(k) % 2 == 1)
+
+
+# ---------------------------------------------------------------------------
+# collect
+# ---------------------------------------------------------------------------
+def _time(fn, stream, budget_ms=30.0, min_reps=3, max_reps=50, rounds=2):
+    """Mean time of `reps` back-to-back calls, the best of `rounds` rounds."""
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    est = max(e0.elapsed_time(e1), 1e-3)
+    reps = int(min(max_reps, max(min_reps, budget_ms / est)))
+    best = None
+    for _ in range(rounds):
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / reps
+        best = t if best is None else min(best, t)
+    return best
+
+
+def collect(path, log=print):
+    import torch
+
+    from . import synth
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    nmax = max(sizes())
+    g = synth.system_device(2024, nmax)
+    dev = {"f64_df": {k: g[k] for k in "abcd"}}
+    dev["f32"] = {k: g[k].float() for k in "abcd"}
+    xs = {"f64_df": torch.empty(nmax, dtype=torch.float64, device="cuda"),
+          "f32": torch.empty(nmax, dtype=torch.float32, device="cuda")}
+    rows = []
+    t0 = time.time()
+    # device-resident single systems: block size
+    for dt in DTYPES:
+        for n in sizes():
+            a, b, c, d = (dev[dt][k][:n] for k in "abcd")
+            x = xs[dt][:n]
+            for m in M_GRID:
+                plan = binding.Plan(n, dtype=dt, m=m, m_reduced=32, flags=binding.TRACE)
+                ms = _time(lambda: plan.solve(a, b, c, d, x, stream=stream), stream)
+                st = plan.query()["stage_ms"]
+                rows.append(dict(kind="device", n=n, batch=1, dtype=DTYPES[dt], residency=0,
+                                 m=m, S=1, chunk=0, ms=ms, s13_ms=st[0] + st[2]))
+                plan.close()
+        log(f"device {dt} done {time.time() - t0:.0f}s")
+    # device-resident batches: block size
+    for dt in DTYPES:
+        for batch in BATCHES:
+            sz = synth.batch_sizes(3000 + batch, batch, 8, 20)
+            off = synth.offsets_from_sizes(sz)
+            n = int(off[-1])
+            gb = synth.system_device(3000 + batch, n, offsets=off)
+            tdt = torch.float32 if dt == "f32" else torch.float64
+            a, b, c, d = (gb[k].to(tdt) for k in "abcd")
+            del gb
+            x = torch.empty(n, dtype=tdt, device="cuda")
+            offs = torch.as_tensor(off, device="cuda")
+            for m in M_GRID:
+                plan = binding.Plan(n, dtype=dt, m=m, m_reduced=32, batch_max=batch)
+                ms = _time(lambda: plan.solve_batched(offs, a, b, c, d, x, host_offsets=off,
+                                                      stream=stream), stream)
+                rows.append(dict(kind="batched", n=n, batch=batch, dtype=DTYPES[dt],
+                                 residency=0, m=m, S=1, chunk=0, ms=ms, s13_ms=0.0))
+                plan.close()
+            del a, b, c, d, x
+        log(f"batched {dt} done {time.time() - t0:.0f}s")
+    # host-resident pipeline: streams and chunk size
+    for dt in DTYPES:
+        hk = {k: dev[dt][k].cpu().pin_memory() for k in "abcd"}
+        hx = torch.empty(nmax, dtype=hk["b"].dtype).pin_memory()
+        for n in sizes():
+            a, b, c, d = (hk[k][:n] for k in "abcd")
+            x = hx[:n]
+            for S in S_GRID:
+                for chunk in CHUNK_GRID:
+                    if chunk and chunk * 2 > n:
+                        continue
+                    plan = binding.Plan(n, dtype=dt, residency="host", m=M_HOST, streams=S,
+                                        chunk=chunk)
+                    ms = _time(lambda: plan.solve_host_async(a, b, c, d, x, stream=stream),
+                               stream, budget_ms=20.0, max_reps=20)
+                    rows.append(dict(kind="host", n=n, batch=1, dtype=DTYPES[dt], residency=1,
+                                     m=M_HOST, S=S, chunk=chunk, ms=ms, s13_ms=0.0))
+                    plan.close()
+        del hk, hx
+        log(f"host {dt} done {time.time() - t0:.0f}s")
+    with open(path, "w", newline="") as f:
+        w = csv.DictWriter(f, fieldnames=FIELDS)
+        w.writeheader()
+        for r in rows:
+            w.writerow(r)
+    return rows
+
+
+def load(path):
+    with open(path) as f:
+        return [{k: (float(v) if k in ("ms", "s13_ms") else (v if k == "kind" else int(v)))
+                 for k, v in r.items()} for r in csv.DictReader(f)]
+
+
+# ---------------------------------------------------------------------------
+# dataset
+# ---------------------------------------------------------------------------
+def points(rows):
+    """Group timings by point (kind, n, batch, dtype, residency)."""
+    pts = {}
+    for r in rows:
+        key = (r["kind"], r["n"], r["batch"], r["dtype"], r["residency"])
+        pts.setdefault(key, []).append(r)
+    return pts
+
+
+def chunk_eff(n, S, chunk):
+    return chunk if chunk > 0 else -(-n // S)
+
+
+def features(n, batch, dtype, residency):
+    return [math.log2(max(n, 2)), math.log2(max(batch, 1)), float(dtype), float(residency)]
+
+
+def target(best):
+    n = best["n"]
+    return [math.log2(best["m"]), math.log2(best["S"]),
+            math.log2(chunk_eff(n, best["S"], best["chunk"]))]
+
+
+def dataset(rows, train=True):
+    X, T, keys = [], [], []
+    for key, recs in sorted(points(rows).items()):
+        if held_out(recs[0]) == train:
+            continue
+        best = min(recs, key=lambda r: r["ms"])
+        X.append(features(key[1], key[2], key[3], key[4]))
+        T.append(target(best))
+        keys.append(key)
+    return np.array(X, dtype=np.float64), np.array(T, dtype=np.float64), keys
+
+
+# ---------------------------------------------------------------------------
+# train (on the GPU, with libtps's kernels)
+# ---------------------------------------------------------------------------
+def _mlp_lib():
+    L = binding.lib()
+    P, I32 = ctypes.c_void_p, ctypes.c_int32
+    L.tps_mlp_workspace_floats.argtypes = [I32]
+    L.tps_mlp_workspace_floats.restype = ctypes.c_size_t
+    L.tps_mlp_forward.argtypes = [P, I32, P, P, P, P]
+    L.tps_mlp_loss_backward.argtypes = [P, I32, P, P, P, P, P, P]
+    L.tps_mlp_adam_step.argtypes = [P, P, P, P, I32, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float, ctypes.c_float, P]
+    for f in ("tps_mlp_forward", "tps_mlp_loss_backward", "tps_mlp_adam_step"):
+        getattr(L, f).restype = ctypes.c_int
+    return L
+
+
+def init_params(seed=0):
+    rng = np.random.default_rng(seed)
+    dims = (4, 64, 64, 3)
+    parts = []
+    for i in range(3):
+        lim = math.sqrt(6.0 / dims[i])
+        parts.append(rng.uniform(-lim, lim, size=(dims[i + 1], dims[i])).ravel())
+        parts.append(np.zeros(dims[i + 1]))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def train(rows, out_path, steps=4000, lr=3e-3, seed=0, log=print):
+    import torch
+
+    X, T, _ = dataset(rows, train=True)
+    fmean = X.mean(axis=0)
+    fstd = X.std(axis=0)
+    fscale = np.where(fstd > 0, 1.0 / np.where(fstd > 0, fstd, 1.0), 1.0)
+    oscale = np.array([10.0, 5.0, 28.0])
+    Xn = ((X - fmean) * fscale).astype(np.float32)
+    Tn = (T / oscale).astype(np.float32)
+    L = _mlp_lib()
+    dev = torch.device("cuda")
+    p = torch.as_tensor(init_params(seed), device=dev)
+    g = torch.zeros_like(p)
+    m1 = torch.zeros_like(p)
+    v1 = torch.zeros_like(p)
+    x = torch.as_tensor(Xn, device=dev)
+    t = torch.as_tensor(Tn, device=dev)
+    B = x.shape[0]
+    work = torch.empty(int(L.tps_mlp_workspace_floats(B)), dtype=torch.float32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    ptr = lambda z: ctypes.c_void_p(z.data_ptr())
+    hist = []
+    for it in range(1, steps + 1):
+        binding.check(L.tps_mlp_loss_backward(ptr(p), B, ptr(x), ptr(t), ptr(g), ptr(loss),
+                                              ptr(work), st), "tps_mlp_loss_backward")
+        lr_t = 0.5 * lr * (1.0 + math.cos(math.pi * (it - 1) / steps))  # cosine decay
+        binding.check(L.tps_mlp_adam_step(ptr(p), ptr(g), ptr(m1), ptr(v1), it, lr_t, 0.9,
+                                          0.999, 1e-8, st), "tps_mlp_adam_step")
+        if it % 500 == 0 or it == 1:
+            hist.append((it, float(loss.item())))
+            log(f"step {it} loss {hist[-1][1]:.3e}")
+    params = p.cpu().numpy()
+    os.makedirs(os.path.dirname(out_path) or ".", exist_ok=True)
+    with open(out_path, "wb") as f:
+        f.write(b"TPSMLP1\0")
+        f.write(struct.pack("<i", params.size))
+        f.write(fmean.astype("<f4").tobytes())
+        f.write(fscale.astype("<f4").tobytes())
+        f.write(oscale.astype("<f4").tobytes())
+        f.write(params.astype("<f4").tobytes())
+    return hist
+
+
+# ---------------------------------------------------------------------------
+# evaluate
+# ---------------------------------------------------------------------------
+def _predict(desc_kw):
+    d = binding.PlanDesc(**desc_kw)
+    m, S, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    L = binding.lib()
+    L.tps_predict_params.argtypes = [ctypes.POINTER(binding.PlanDesc), ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_void_p]
+    L.tps_predict_params.restype = ctypes.c_int
+    rc = L.tps_predict_params(ctypes.byref(d), ctypes.byref(m), ctypes.byref(S),
+                              ctypes.byref(c))
+    if rc != 0:
+        raise RuntimeError("predictor weights not loaded")
+    return m.value, S.value, c.value
+
+
+def _lookup(recs, m=None, S=None, chunk=None):
+    """Time of the grid configuration nearest the requested one; records
+    that describe the same configuration (a chunk of n/S rows given as 0 or
+    explicitly) count as one, at their best time."""
+    def cfg(r):
+        return (r["m"], r["S"], chunk_eff(r["n"], r["S"], r["chunk"]))
+
+    def dist(r):
+        dm, dS, dc = cfg(r)
+        v = 0.0
+        if m is not None:
+            v += abs(math.log2(dm) - math.log2(m))
+        if S is not None:
+            v += abs(math.log2(dS) - math.log2(S))
+        if chunk is not None:
+            v += 1e-3 * abs(math.log2(dc) - math.log2(chunk_eff(r["n"], S or dS, chunk)))
+        return v
+
+    dmin = min(dist(r) for r in recs)
+    near = [r for r in recs if dist(r) == dmin]
+    c0 = cfg(near[0])
+    return min(r["ms"] for r in recs if cfg(r) == c0)
+
+
+def paper_rule_coeffs(rows):
+    """Eq. 4 and Eq. 7 refit on this GPU's training timings (fp64, host
+    pipeline, one chunk per stream): sum = the Stage-1 + Stage-3 kernel time
+    at m = 128 (the work the streams overlap), T_overhead from Eq. 5."""
+    sums = {}
+    for r in rows:
+        if r["kind"] == "device" and r["m"] == M_HOST and not held_out(r):
+            sums[(r["n"], r["dtype"])] = r["s13_ms"]
+    xs, ys = [], []
+    for (n, dt), s in sums.items():
+        if dt == 0:
+            xs.append(n)
+            ys.append(s)
+    A = np.stack([np.array(xs, float), np.ones(len(xs))], axis=1)
+    k_sum, q_sum = np.linalg.lstsq(A, np.array(ys), rcond=None)[0]
+    small, big = [], []
+    for key, recs in points(rows).items():
+        kind, n, batch, dt, res = key
+        if kind != "host" or dt != 0 or held_out(recs[0]):
+            continue
+        t1 = [r["ms"] for r in recs if r["S"] == 1 and r["chunk"] == 0]
+        if not t1:
+            continue
+        s = k_sum * n + q_sum
+        for r in recs:
+            if r["chunk"] == 0 and r["S"] > 1:
+                ov = (r["ms"] - t1[0]) + (r["S"] - 1) / r["S"] * s  # Eq. 5
+                (small if n <= 1e6 else big).append((n, r["S"], ov))
+    def lsq(cols, y):
+        return np.linalg.lstsq(np.stack(cols, axis=1), np.array(y), rcond=None)[0]
+    sm = np.array([x[0] for x in small], float)
+    ss = np.array([x[1] for x in small], float)
+    co_small = lsq([sm, np.log10(ss), np.ones_like(sm)], [x[2] for x in small])
+    bn = np.array([x[0] for x in big], float)
+    bs = (4.0 / 3.0) * np.log2(np.array([x[1] for x in big], float))
+    co_big = lsq([bn * bs, bs, np.ones_like(bn)], [x[2] for x in big])
+    return np.array([k_sum, q_sum]), co_small, co_big
+
+
+def paper_rule_streams(n, coeffs):
+    L = binding.lib()
+    L.tps_paper_predict_streams.argtypes = [ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_double]
+    L.tps_paper_predict_streams.restype = ctypes.c_int32
+    s, sm, bg = (np.ascontiguousarray(c, dtype=np.float64) for c in coeffs)
+    return int(L.tps_paper_predict_streams(float(n), s.ctypes.data, sm.ctypes.data,
+                                           bg.ctypes.data, 1e6))
+
+
+def default_params(n, residency):
+    m = 128
+    while m > 8 and n // m < 152 * 32 * 4:
+        m //= 2
+    return m, (4 if residency else 1), 0
+
+
+def evaluate(rows, weights_path):
+    L = binding.lib()
+    L.tps_predict_load.argtypes = [ctypes.c_char_p]
+    if L.tps_predict_load(weights_path.encode()) != 0:
+        raise RuntimeError(f"cannot load {weights_path}")
+    coeffs = paper_rule_coeffs(rows)
+    res = {"mlp": [], "paper_rule": [], "defaults": []}
+    detail = []
+    for key, recs in sorted(points(rows).items()):
+        if not held_out(recs[0]):
+            continue
+        kind, n, batch, dt, resid = key
+        tbest = min(r["ms"] for r in recs)
+        pm, pS, pc = _predict(dict(n_max=n, batch_max=batch if batch > 1 else 0,
+                                   dtype=(1 if dt == 1 else 3), residency=resid))
+        dm, dS, dc = default_params(n, resid)
+        if kind == "host":
+            t_mlp = _lookup(recs, S=pS, chunk=pc)
+            t_def = _lookup(recs, S=dS, chunk=dc)
+            t_pap = _lookup(recs, S=paper_rule_streams(n, coeffs), chunk=0)
+        else:
+            t_mlp = _lookup(recs, m=pm)
+            t_def = _lookup(recs, m=dm)
+            t_pap = t_def  # the paper's rule chooses only S
+        res["mlp"].append(t_mlp / tbest - 1)
+        res["defaults"].append(t_def / tbest - 1)
+        res["paper_rule"].append(t_pap / tbest - 1)
+        detail.append(dict(kind=kind, n=n, batch=batch, dtype=dt, best_ms=tbest,
+                           mlp=t_mlp / tbest - 1, defaults=t_def / tbest - 1,
+                           paper_rule=t_pap / tbest - 1, pred=(pm, pS, pc)))
+    summary = {k: {"mean": float(np.mean(v)), "max": float(np.max(v)), "points": len(v)}
+               for k, v in res.items()}
+    return summary, detail, coeffs
+
+
+def main(argv):
+    cmd = argv[1] if len(argv) > 1 else "all"
+    out = argv[2] if len(argv) > 2 else PRED_DIR
+    os.makedirs(out, exist_ok=True)
+    csv_path = os.path.join(out, "timings_gb300.csv")
+    w_path = os.path.join(out, "weights.bin")
+    if cmd in ("collect", "all"):
+        collect(csv_path)
+    rows = load(csv_path)
+    if cmd in ("train", "all"):
+        hist = train(rows, w_path)
+        with open(os.path.join(out, "train_log.json"), "w") as f:
+            json.dump(hist, f)
+    if cmd in ("evaluate", "all"):
+        summary, detail, coeffs = evaluate(rows, w_path)
+        with open(os.path.join(out, "regret.json"), "w") as f:
+            json.dump({"summary": summary, "detail": detail,
+                       "paper_rule_coeffs": [list(map(float, c)) for c in coeffs]}, f, indent=1)
+        print(json.dumps(summary))
+
+
+if __name__ == "__main__":
+    main(sys.argv)
