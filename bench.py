@@ -55,6 +55,7 @@ def args_():
     p.add_argument("--chunk", type=int, default=0)
     p.add_argument("--e2e-steps", type=int, default=0)
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-extra", action="store_true", help="skip the batched and mixed lines")
     return p.parse_args()
 
 
@@ -67,8 +68,19 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def kernel_source_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    for fn in ("partition_kernels.cuh", "arith.cuh"):
+        with open(os.path.join(ROOT, "paper_2501_05938_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_table():
-    """Per-row DRAM bytes of each kernel from the committed ncu summary."""
+    """Per-row DRAM bytes of each kernel from the committed ncu summary, used
+    only while the kernel sources still hash to what was profiled."""
     out = {}
     path = os.path.join(ROOT, "profiles", "dram_traffic_per_row.txt")
     if os.path.exists(path):
@@ -76,8 +88,9 @@ def traffic_table():
             for line in f:
                 if line.startswith("#") or not line.strip():
                     continue
-                k, v = line.split()[:2]
-                out[k] = float(v)
+                k, v, hsh = line.split()[:3]
+                if hsh == kernel_source_hash():
+                    out[k] = float(v)
     return out
 
 
@@ -161,14 +174,22 @@ def barrier(world):
 
 
 def max_over_ranks(v, world):
+    """The slowest rank's time (the job's time); host-side, any backend."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(rows_per_rank, world, ms):
+    """Whole-job throughput: every rank solved its own system of
+    rows_per_rank rows; ms is the slowest rank's time per step."""
+    return world * rows_per_rank / (ms * 1e-3)
 
 
 def time_device(plan, g, x, steps, warmup, world, stream):
@@ -268,6 +289,69 @@ def reference_arm(a):
     print(json.dumps(line), flush=True)
 
 
+def extra_workloads(binding, synth, world, rank, stream, a):
+    """Throughput of the other two workloads, reported beside the headline:
+    4096 packed systems with n_i log-uniform in [2^8, 2^20] (tuned, fp32 and
+    plain fp64) and the mixed-precision refinement of an n = 2^27 system
+    with dominance ratio 1.01."""
+    import torch
+
+    out = {}
+    sizes = synth.batch_sizes(1003 + rank, 4096, 8, 20)
+    off = synth.offsets_from_sizes(sizes)
+    nb = int(off[-1])
+    gb = synth.system_device(1003 + rank, nb, offsets=off)
+    offs = torch.as_tensor(off, device="cuda")
+    res = {"systems": 4096, "rows": nb}
+    for dt in ("f64_df", "f32", "f64"):
+        tdt = torch.float32 if dt == "f32" else torch.float64
+        arrs = [gb[k].to(tdt) for k in "abcd"]
+        x = torch.empty(nb, dtype=tdt, device="cuda")
+        plan = binding.Plan(nb, dtype=dt, batch_max=4096, flags=binding.TUNE_PREDICT)
+        steps = max(3, a.steps // 10)
+        for _ in range(2):
+            plan.solve_batched(offs, *arrs, x, host_offsets=off, stream=stream)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            plan.solve_batched(offs, *arrs, x, host_offsets=off, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps, world)
+        err = ((x.double() - gb["x_true"]).abs().max() / gb["x_true"].abs().max()).item()
+        res[dt] = {"value": world * nb / (ms * 1e-3), "ms_per_step": ms,
+                   "m": plan.query()["m"], "rel_fwd_vs_x_true": err}
+        del arrs, x, plan
+    out["batched"] = res
+    del gb, offs
+    n = a.n
+    g = synth.system_device(1005 + rank, n, kind=synth.KIND_RATIO, ratio=1.01)
+    x = torch.empty_like(g["b"])
+    mres = {"n": n, "ratio": 1.01}
+    for dt in ("mixed", "f64_df", "f64"):
+        plan = binding.Plan(n, dtype=dt, flags=binding.TUNE_PREDICT)
+        plan.solve(g["a"], g["b"], g["c"], g["d"], x, stream=stream)
+        stream.synchronize()
+        steps = 3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            plan.solve(g["a"], g["b"], g["c"], g["d"], x, stream=stream)
+        e1.record(stream)
+        stream.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps, world)
+        q = plan.query()
+        err = ((x - g["x_true"]).abs().max() / g["x_true"].abs().max()).item()
+        mres[dt] = {"value": world * n / (ms * 1e-3), "ms_per_step": ms,
+                    "iterations": q["iterations"], "status": q["status_name"],
+                    "rel_fwd_vs_x_true": err}
+        del plan
+    out["mixed"] = mres
+    del g, x
+    return out
+
+
 def main():
     a = args_()
     if a.impl == "reference":
@@ -288,9 +372,9 @@ def main():
     hbm_peak, peak_kind = peaks()
     out = {}
     with Clocks(dev) as clk:
-        # tuned: double-float arithmetic
+        # tuned: double-float arithmetic, launch parameters from the predictor
         plan = binding.Plan(n, dtype="f64_df", m=a.m, m_reduced=a.m_reduced,
-                            flags=binding.TRACE)
+                            flags=binding.TRACE | binding.TUNE_PREDICT | binding.GRAPH)
         ms, info = time_device(plan, g, x, a.steps, a.warmup, world, stream)
         err_true, res = verify(g, x)
         # plain: native fp64 arithmetic
@@ -304,7 +388,7 @@ def main():
         hk = {k: g[k].cpu().pin_memory() for k in "abcd"}
         hx = torch.empty(n, dtype=torch.float64).pin_memory()
         plan_h = binding.Plan(n, dtype="f64_df", residency="host", m=a.m, m_reduced=a.m_reduced,
-                              streams=a.streams, chunk=a.chunk)
+                              streams=a.streams, chunk=a.chunk, flags=binding.TUNE_PREDICT)
         esteps = a.e2e_steps or max(3, min(a.steps, 20))
         for _ in range(min(a.warmup, 3)):
             plan_h.solve_host_async(hk["a"], hk["b"], hk["c"], hk["d"], hx, stream=stream)
@@ -320,15 +404,20 @@ def main():
         ems = max_over_ranks(e0.elapsed_time(e1) / esteps, world)
         infoh = plan_h.query()
         eh_err = (hx.to("cuda") - g["x_true"]).abs().max().item() / g["x_true"].abs().max().item()
+        del hk, hx, plan_h
+        extra = {}
+        if not a.no_extra:
+            extra = extra_workloads(binding, synth, world, rank, stream, a)
     clocks = clk.summary()
 
-    value = world * n / (ms * 1e-3)
+    value = job_value(n, world, ms)
     s1, s2, s3, tot = info["stage_ms"]
     dominant = "k_stage1" if s1 >= s3 else "k_stage3"
     dom_ms = max(s1, s3)
     alg_bytes = (32 if dominant == "k_stage1" else 40) * n
     achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
     traffic = traffic_table().get(f"{dominant}_f64_df")
+    kernel_hash = kernel_source_hash()
     levels = info["levels"]
     launches_per_step = 2 * levels + 1
     line = {
@@ -350,13 +439,14 @@ def main():
                      "unit": "GB/s", "frac": achieved / hbm_peak,
                      "traffic": (traffic * n if traffic else None),
                      "peak_kind": peak_kind,
-                     "alg_bytes_per_row": alg_bytes // n},
+                     "alg_bytes_per_row": alg_bytes // n, "kernel_source": kernel_hash},
         "e2e": {"value": world * n / (ems * 1e-3), "unit": UNIT, "ms_per_step": ems,
                 "steps": esteps, "h2d_bytes_per_step": 4 * 8 * n, "d2h_bytes_per_step": 8 * n,
                 "streams": infoh["streams"], "chunk": infoh["chunk"],
                 "rel_fwd_vs_x_true": eh_err},
         "clocks": clocks,
     }
+    line.update(extra)
     if rank == 0 and world == 1 and not a.no_cpu:
         cpu, err_o, res_o, _ = cpu_oracle_leg(g, x)
         line["cpu_baseline"] = cpu

@@ -71,6 +71,7 @@ typedef enum {
 #define TPS_TUNE_EXHAUSTIVE 2u    /* time the candidate grid on the device        */
 #define TPS_TRACE 4u              /* record per-stage event times (tps_plan_query) */
 #define TPS_EXTERNAL_WORKSPACE 8u /* caller supplies the workspace                */
+#define TPS_GRAPH 16u             /* replay Stage 2 as one CUDA graph launch      */
 
 typedef struct {
   int64_t n_max;     /* largest n of tps_solve / tps_solve_host_async, or the  */
@@ -126,7 +127,13 @@ tps_status tps_set_workspace(tps_plan_t plan, void* dev_ptr, size_t bytes);
  * Stages 1-3 on the GPU).  a, b, c, d, x: device pointers to n elements of
  * the plan's I/O type, 8-byte aligned for fp64, 4-byte for fp32.  Enqueues
  * the kernels on `stream` and returns; no host synchronisation, so it may
- * be captured into a CUDA graph. */
+ * be captured into a CUDA graph (except TPS_MIXED_F32_F64, which reads its
+ * convergence test back to the host after every correction).  With
+ * TPS_GRAPH the plan captures Stage 2 -- the recursive solve of the reduced
+ * system, a chain of small launches that touches only the workspace -- into
+ * a CUDA graph on a private stream at the first solve with a given level
+ * geometry, and replays it as one graph launch afterwards (also from
+ * tps_solve_batched and the host pipeline). */
 tps_status tps_solve(tps_plan_t plan, int64_t n, const void* a, const void* b, const void* c,
                      const void* d, void* x, void* stream);
 

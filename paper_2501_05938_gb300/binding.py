@@ -18,7 +18,7 @@ STATUS = {0: "TPS_OK", 1: "TPS_ERR_INVALID_ARG", 2: "TPS_ERR_UNSUPPORTED", 3: "T
           7: "TPS_ERR_TIMEOUT"}
 DTYPES = {"f64": 0, "f32": 1, "mixed": 2, "f64_df": 3}
 RESIDENCY = {"device": 0, "host": 1}
-TUNE_PREDICT, TUNE_EXHAUSTIVE, TRACE, EXTERNAL_WORKSPACE = 1, 2, 4, 8
+TUNE_PREDICT, TUNE_EXHAUSTIVE, TRACE, EXTERNAL_WORKSPACE, GRAPH = 1, 2, 4, 8, 16
 
 # every symbol include/tps.h declares
 EXPORTS = ("tps_plan", "tps_plan_destroy", "tps_workspace_size", "tps_set_workspace", "tps_solve",

@@ -31,9 +31,12 @@ struct ArF64 {
   __device__ __forceinline__ static T one() { return 1.0; }
   __device__ __forceinline__ static T mul(T x, T y) { return x * y; }
   __device__ __forceinline__ static T mul_nn(T x, T y) { return x * y; }
+  __device__ __forceinline__ static T mul_neg_nn(T x, T y) { return -(x * y); }
+  __device__ __forceinline__ static T norm(T x) { return x; }
   // x - y*z, one rounding
   __device__ __forceinline__ static T sub_mul(T x, T y, T z) { return fma(-y, z, x); }
   __device__ __forceinline__ static T sub_mul_dom(T x, T y, T z) { return fma(-y, z, x); }
+  __device__ __forceinline__ static T sub_mul_nn(T x, T y, T z) { return fma(-y, z, x); }
   __device__ __forceinline__ static T neg(T x) { return -x; }
   // Newton-Raphson iteration for r = 1/x (r <- r + r(1 - x r)), seeded by
   // the hardware approximation rcp.approx.ftz.f64 and applied twice; each
@@ -60,8 +63,11 @@ struct ArF32 {
   __device__ __forceinline__ static T one() { return 1.0f; }
   __device__ __forceinline__ static T mul(T x, T y) { return __fmul_rn(x, y); }
   __device__ __forceinline__ static T mul_nn(T x, T y) { return __fmul_rn(x, y); }
+  __device__ __forceinline__ static T mul_neg_nn(T x, T y) { return __fmul_rn(-x, y); }
+  __device__ __forceinline__ static T norm(T x) { return x; }
   __device__ __forceinline__ static T sub_mul(T x, T y, T z) { return fmaf(-y, z, x); }
   __device__ __forceinline__ static T sub_mul_dom(T x, T y, T z) { return fmaf(-y, z, x); }
+  __device__ __forceinline__ static T sub_mul_nn(T x, T y, T z) { return fmaf(-y, z, x); }
   __device__ __forceinline__ static T neg(T x) { return -x; }
   // hardware reciprocal approximation refined by one Newton-Raphson step
   __device__ __forceinline__ static T rcp(T x) {
@@ -154,6 +160,32 @@ struct ArDF {
     e = fmaf(x.hi, y.lo, e);
     e = fmaf(x.lo, y.hi, e);
     return {p, e};
+  }
+  // -(x*y) as an unevaluated pair; the negation rides on the operands.
+  __device__ __forceinline__ static T mul_neg_nn(T x, T y) {
+    const float p = __fmul_rn(-x.hi, y.hi);
+    float e = fmaf(-x.hi, y.hi, -p);
+    e = fmaf(-x.hi, y.lo, e);
+    e = fmaf(-x.lo, y.hi, e);
+    return {p, e};
+  }
+  // Renormalise a pair (Fast2Sum) so that |lo| <= ulp(hi) / 2.
+  __device__ __forceinline__ static T norm(T x) {
+    T r;
+    fast_two_sum(x.hi, x.lo, r.hi, r.lo);
+    return r;
+  }
+  // x - y*z without the final renormalisation: the pair (s, se) is exact
+  // up to the product's rounding, but |se| may exceed ulp(s) / 2.  Safe for
+  // a few steps of an accumulator that is renormalised periodically.
+  __device__ __forceinline__ static T sub_mul_nn(T x, T y, T z) {
+    const float p = __fmul_rn(y.hi, z.hi);
+    float pe = fmaf(y.hi, z.hi, -p);
+    pe = fmaf(y.hi, z.lo, pe);
+    pe = fmaf(y.lo, z.hi, pe);
+    float s, se;
+    two_sum(x.hi, -p, s, se);
+    return {s, __fadd_rn(se, __fsub_rn(x.lo, pe))};
   }
   // x - y*z: the product is formed as an unevaluated pair (p, pe), then
   // TwoSum of the high parts and a final Fast2Sum.

@@ -291,20 +291,28 @@ __global__ void __launch_bounds__(W * 32)
   T beta = Ar::one(), clast = Ar::zero();
   bool bad = false;
 
-  // one interior row (1 <= row <= L-2)
+  // one interior row (1 <= row <= L-2).  The product chains alpha and S and
+  // the accumulators P and Q are left unnormalised here and renormalised
+  // once per chunk (renorm), which bounds their low parts to a few ulps.
   auto interior = [&](const T av, const T bv, const T cv, const T dv) {
     const T ratio = Ar::mul_nn(av, rbp);
     beta = Ar::sub_mul_dom(bv, ratio, cprev);
     g = Ar::sub_mul(dv, ratio, g);
-    al = Ar::neg(Ar::mul(ratio, al));
+    al = Ar::mul_neg_nn(ratio, al);
     bad |= Ar::bad_pivot(beta);
     const T rbeta = Ar::rcp(beta);
     const T tt = Ar::mul_nn(S, rbeta);
-    P = Ar::sub_mul(P, tt, g);
-    Q = Ar::sub_mul(Q, tt, al);
-    S = Ar::neg(Ar::mul(tt, cv));
+    P = Ar::sub_mul_nn(P, tt, g);
+    Q = Ar::sub_mul_nn(Q, tt, al);
+    S = Ar::mul_neg_nn(tt, cv);
     rbp = rbeta;
     cprev = cv;
+  };
+  auto renorm = [&]() {
+    al = Ar::norm(al);
+    S = Ar::norm(S);
+    P = Ar::norm(P);
+    Q = Ar::norm(Q);
   };
 
   for (int ch = 0; ch < nch; ++ch) {
@@ -344,12 +352,13 @@ __global__ void __launch_bounds__(W * 32)
             const T ratio = Ar::mul_nn(av, rbp);
             beta = Ar::sub_mul_dom(bv, ratio, cprev);
             g = Ar::sub_mul(dv, ratio, g);
-            al = Ar::neg(Ar::mul(ratio, al));
+            al = Ar::mul_neg_nn(ratio, al);
             clast = cv;
           }
         }
       }
     }
+    renorm();
     // checkpoint after every K rows, when the next K rows start with an
     // interior row (Stage 3 restarts its K-row chunk there)
     if (active && ((row0 + R) % K) == 0 && row0 + R <= L - 2) {

@@ -250,6 +250,44 @@ cudaError_t base_solve(tps_plan_s* P, int64_t n, const void* a, const void* b, c
   });
 }
 
+// TPS_GRAPH: Stage 2 (every level below the top, many small launches)
+// touches only workspace buffers, so one captured graph serves every solve
+// with the same level geometry; it is replayed as a single launch.
+cudaError_t reduced_solve_graph(tps_plan_s* P, const std::vector<LevelPlan>& levels,
+                                cudaStream_t s) {
+  const Level& L0 = levels[0].lv;
+  const int64_t key[12] = {2 * L0.p, (int64_t)levels.size(), P->m_reduced, (int64_t)P->ws,
+                           P->desc.dtype, (int64_t)levels[0].off_red[0], 0, 0, 0, 0, 0, 0};
+  bool same = P->graph != nullptr;
+  for (int i = 0; i < 12 && same; ++i) same = P->gkey[i] == key[i];
+  if (!same) {
+    if (P->graph) {
+      cudaGraphExecDestroy(P->graph);
+      P->graph = nullptr;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!P->cap_stream) e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const cudaError_t ec = reduced_solve(P, levels, P->cap_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(P->cap_stream, &g);
+    if (ec != cudaSuccess || e != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return ec != cudaSuccess ? ec : (e != cudaSuccess ? e : cudaErrorUnknown);
+    }
+    e = cudaGraphInstantiate(&P->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      P->graph = nullptr;
+      return e;
+    }
+    for (int i = 0; i < 12; ++i) P->gkey[i] = key[i];
+  }
+  return cudaGraphLaunch(P->graph, s);
+}
+
 tps_status run_solve(tps_plan_s* P, int64_t n, const void* a, const void* b, const void* c,
                      const void* d, void* x, cudaStream_t s, const std::vector<LevelPlan>& lv,
                      cudaEvent_t* ev, const int64_t* bnd, int64_t nbnd) {
@@ -262,7 +300,8 @@ tps_status run_solve(tps_plan_s* P, int64_t n, const void* a, const void* b, con
   } else {
     if (e == cudaSuccess) e = stage1_range(P, lv[0], 0, lv[0].lv.p, a, b, c, d, s);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
-    if (e == cudaSuccess) e = reduced_solve(P, lv, s);
+    if (e == cudaSuccess)
+      e = (P->desc.flags & TPS_GRAPH) ? reduced_solve_graph(P, lv, s) : reduced_solve(P, lv, s);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
     if (e == cudaSuccess) e = stage3_range(P, lv[0], 0, lv[0].lv.p, a, b, c, d, x, s);
   }

@@ -109,7 +109,8 @@ tps_status tps_plan(const tps_plan_desc* desc, tps_plan_t* out) {
   if (d.m_reduced != 0 && (d.m_reduced < 4 || d.m_reduced > (1 << 20))) return TPS_ERR_INVALID_ARG;
   if (d.streams != 0 && (d.streams < 1 || d.streams > 32)) return TPS_ERR_INVALID_ARG;
   if (d.chunk < 0 || d.max_iters < 0 || d.tol < 0.0) return TPS_ERR_INVALID_ARG;
-  if (d.flags & ~(TPS_TUNE_PREDICT | TPS_TUNE_EXHAUSTIVE | TPS_TRACE | TPS_EXTERNAL_WORKSPACE))
+  if (d.flags & ~(TPS_TUNE_PREDICT | TPS_TUNE_EXHAUSTIVE | TPS_TRACE | TPS_EXTERNAL_WORKSPACE |
+                  TPS_GRAPH))
     return TPS_ERR_INVALID_ARG;
 
   tps_plan_s* P = new (std::nothrow) tps_plan_s();
@@ -223,6 +224,8 @@ tps_status tps_plan_destroy(tps_plan_t P) {
       if (P->trace_ev[i]) cudaEventDestroy(P->trace_ev[i]);
     delete[] P->trace_ev;
   }
+  if (P->graph) cudaGraphExecDestroy(P->graph);
+  if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   if (P->ws_owned && P->ws) cudaFree(P->ws);
   if (P->d_work) cudaFree(P->d_work);
   delete P;
@@ -425,7 +428,9 @@ tps_status tps_solve_host_async(tps_plan_t P, int64_t n, const void* a, const vo
     e = cudaEventRecord(H->ev_done1[i], H->streams[i]);
     if (e == cudaSuccess && i > 0) e = cudaStreamWaitEvent(H->streams[0], H->ev_done1[i], 0);
   }
-  if (e == cudaSuccess) e = reduced_solve(P, lv, H->streams[0]);
+  if (e == cudaSuccess)
+    e = (P->desc.flags & TPS_GRAPH) ? reduced_solve_graph(P, lv, H->streams[0])
+                                    : reduced_solve(P, lv, H->streams[0]);
   if (e == cudaSuccess) e = cudaEventRecord(H->ev_red, H->streams[0]);
   for (int i = 1; i < S && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(H->streams[i], H->ev_red, 0);
   // Stage 3 per chunk, then its download

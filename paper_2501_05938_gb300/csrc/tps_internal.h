@@ -67,6 +67,10 @@ struct tps_plan_s {
   cudaEvent_t* trace_ev = nullptr;
   int32_t trace_slots = 0;
   int64_t trace_count = 0;
+  // TPS_GRAPH: the captured solve and the arguments it was captured with
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int64_t gkey[12] = {};
   // batched work list (device) and its capacity in entries
   void* d_work = nullptr;
   size_t work_cap = 0;
@@ -94,6 +98,9 @@ cudaError_t stage3_range(tps_plan_s* P, const LevelPlan& L, int64_t kb, int64_t 
                          const void* a, const void* b, const void* c, const void* d, void* x,
                          cudaStream_t s);
 cudaError_t reduced_solve(tps_plan_s* P, const std::vector<LevelPlan>& levels, cudaStream_t s);
+// The same, captured once into a CUDA graph (TPS_GRAPH) and replayed.
+cudaError_t reduced_solve_graph(tps_plan_s* P, const std::vector<LevelPlan>& levels,
+                                cudaStream_t s);
 cudaError_t base_solve(tps_plan_s* P, int64_t n, const void* a, const void* b, const void* c,
                        const void* d, void* x, cudaStream_t s, const int64_t* bnd = nullptr,
                        int64_t nbnd = 0);

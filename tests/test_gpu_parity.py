@@ -245,3 +245,43 @@ def test_unaligned_arrays_take_the_direct_path(dtype):
     ref = oracle.thomas(a, b, c, d)
     tol = F32_FWD if dtype == "f32" else F64_FWD
     assert oracle.rel_forward_error(views[4].cpu().numpy().astype(np.float64), ref) <= tol
+
+
+def test_graph_mode_replays_and_recaptures():
+    n = 300001
+    plan = binding.Plan(n, dtype="f64_df", flags=binding.GRAPH | binding.TRACE)
+    bufs = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(5)]
+    for seed in (1, 2):  # same pointers, new data: replay
+        s = synth.system(seed, n)
+        for t, k in zip(bufs, "abcd"):
+            t.copy_(torch.as_tensor(s[k]))
+        plan.solve(*bufs)
+        torch.cuda.synchronize()
+        ref = oracle.thomas(s["a"], s["b"], s["c"], s["d"])
+        assert oracle.rel_forward_error(bufs[4].cpu().numpy(), ref) <= F64_FWD
+    info = plan.query()
+    assert info["status"] == 0 and info["stage_ms"][3] > 0
+    s = synth.system(3, n - 5)  # new n and pointers: recapture
+    a, b, c, d = (torch.as_tensor(s[k]).cuda() for k in "abcd")
+    x = torch.empty_like(b)
+    plan.solve(a, b, c, d, x)
+    torch.cuda.synchronize()
+    ref = oracle.thomas(s["a"], s["b"], s["c"], s["d"])
+    assert oracle.rel_forward_error(x.cpu().numpy(), ref) <= F64_FWD
+
+
+def test_graph_mode_batched():
+    sizes = [1000, 1, 0, 4097, 300]
+    off = synth.offsets_from_sizes(sizes)
+    n = int(off[-1])
+    s = synth.system(9, n, offsets=off)
+    a, b, c, d = (torch.as_tensor(s[k]).cuda() for k in "abcd")
+    x = torch.empty_like(b)
+    plan = binding.Plan(n, dtype="f64_df", batch_max=8, flags=binding.GRAPH)
+    offs = torch.as_tensor(off, device="cuda")
+    for _ in range(3):
+        x.zero_()
+        plan.solve_batched(offs, a, b, c, d, x, host_offsets=off)
+        torch.cuda.synchronize()
+        ref = oracle.thomas_batched(off, s["a"], s["b"], s["c"], s["d"])
+        assert oracle.rel_forward_error(x.cpu().numpy(), ref) <= F64_FWD
