@@ -11,7 +11,12 @@ Stage 2, Stage 3).
            (double-float arithmetic on the fp32 pipes, fp64 I/O)
   plain    the same with native fp64 arithmetic (the plain partition solve)
   e2e      tps_solve_host_async from pinned host buffers: chunked H2D,
-           kernels and D2H on the plan's streams, all inside the timed region
+           kernels and D2H on the plan's streams, all inside the timed region;
+           link_floor_ms is the same bytes moved as plain copies (H2D, then
+           D2H) in the same run, the bound no pipeline can beat
+  batched  4096 packed systems, n_i log-uniform in [2^8, 2^20] (--no-extra
+           skips this and the next)
+  mixed    the refinement workload (b = 1.01 (|a| + |c|)) in every arithmetic
   roofline the dominant kernel's algorithmic bytes over its mean duration
            (CUDA events recorded by the library on the launch stream during
            the timed steps) against the measured HBM copy bandwidth
@@ -215,6 +220,28 @@ def time_device(plan, g, x, steps, warmup, world, stream):
     return max_over_ranks(ms, world), info
 
 
+def link_floor(hk, hx, g, x, stream, reps=3):
+    """The host link's floor for one end-to-end step: the step's H2D bytes
+    (a, b, c, d) then its D2H bytes (x) as plain copies on one stream.  No
+    part of x can leave before every input has arrived (the reduced system
+    couples all rows), so the two phases cannot overlap.  Copying g's own
+    values back into g leaves the system unchanged."""
+    import torch
+
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            for k in "abcd":
+                g[k].copy_(hk[k], non_blocking=True)
+            hx.copy_(x, non_blocking=True)
+        e1.record(stream)
+        stream.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
 def verify(g, x):
     """Error against the manufactured solution and the fp64 residual, on the
     device with plain PyTorch ops (verification only)."""
@@ -404,6 +431,7 @@ def main():
         ems = max_over_ranks(e0.elapsed_time(e1) / esteps, world)
         infoh = plan_h.query()
         eh_err = (hx.to("cuda") - g["x_true"]).abs().max().item() / g["x_true"].abs().max().item()
+        floor_ms = link_floor(hk, hx, g, x, stream)
         del hk, hx, plan_h
         extra = {}
         if not a.no_extra:
@@ -443,6 +471,7 @@ def main():
         "e2e": {"value": world * n / (ems * 1e-3), "unit": UNIT, "ms_per_step": ems,
                 "steps": esteps, "h2d_bytes_per_step": 4 * 8 * n, "d2h_bytes_per_step": 8 * n,
                 "streams": infoh["streams"], "chunk": infoh["chunk"],
+                "link_floor_ms": floor_ms, "frac_of_link_floor": floor_ms / ems,
                 "rel_fwd_vs_x_true": eh_err},
         "clocks": clocks,
     }

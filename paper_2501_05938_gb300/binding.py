@@ -10,7 +10,7 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libtps.so")
+LIB_PATH = os.environ.get("TPS_LIB_PATH") or os.path.join(HERE, "libtps.so")
 
 TPS_OK = 0
 STATUS = {0: "TPS_OK", 1: "TPS_ERR_INVALID_ARG", 2: "TPS_ERR_UNSUPPORTED", 3: "TPS_ERR_CUDA",

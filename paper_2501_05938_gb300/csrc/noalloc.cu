@@ -107,7 +107,7 @@ cudaError_t run(unsigned char* ws, const Layout& L, int idx, int64_t n, const Ti
   }
   const LevelPlan& P = L.lv[idx];
   constexpr int K = sizeof(Tin) >= 8 ? 8 : 16;  // Stage-3 chunk rows, checkpoint spacing
-  constexpr int R1 = K / 2;
+  constexpr int R1 = K;
   Tred* red[5];
   for (int i = 0; i < 5; ++i) red[i] = reinterpret_cast<Tred*>(ws + P.off_red[i]);
   Tred* ck[3];

@@ -249,8 +249,8 @@ __device__ __forceinline__ int warp_lmin(const Level& lv, int64_t k0, int nb) {
 }
 
 // ------------------------------------------------------------------ Stage 1
-// R rows per chunk; a checkpoint every K rows (K a multiple of R, and the
-// chunk length of Stage 3).
+// R rows per chunk; a checkpoint every K rows (K the chunk length of
+// Stage 3; one of R and K divides the other).
 template <class Ar, class Tin, class Tred, int R, int K, int W, bool kVec16>
 __global__ void __launch_bounds__(W * 32)
     k_stage1(Level lv, const Tin* __restrict__ a, const Tin* __restrict__ b,
@@ -261,6 +261,7 @@ __global__ void __launch_bounds__(W * 32)
   using T = typename Ar::T;
   using TL = Tile<Tin, R>;
   constexpr int V = TL::kVec;
+  static_assert(R % K == 0 || K % R == 0, "chunk rows and checkpoint spacing must nest");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t k0 = lv.k_begin + ((int64_t)blockIdx.x * W + warp) * 32;
@@ -314,6 +315,16 @@ __global__ void __launch_bounds__(W * 32)
     P = Ar::norm(P);
     Q = Ar::norm(Q);
   };
+  // checkpoint after row `row` (a multiple of K minus one), when the next K
+  // rows start with an interior row (Stage 3 restarts its chunk there)
+  auto checkpoint = [&](int row) {
+    if (active && row + 1 <= L - 2) {
+      const int64_t slot = (int64_t)((row + 1) / K - 1) * lv.p + k;
+      Ar::to(ck_gam[slot], Ar::mul(cprev, rbp));
+      Ar::to(ck_y[slot], Ar::mul(Ar::norm(g), rbp));
+      Ar::to(ck_v[slot], Ar::mul(Ar::norm(al), rbp));
+    }
+  };
 
   for (int ch = 0; ch < nch; ++ch) {
     const int row0 = ch * R;
@@ -330,8 +341,12 @@ __global__ void __launch_bounds__(W * 32)
         const Vec16<Tin> xa = lds16(t + r), xb = lds16(t + TL::kArr + r),
                          xc = lds16(t + 2 * TL::kArr + r), xd = lds16(t + 3 * TL::kArr + r);
 #pragma unroll
-        for (int v = 0; v < V; ++v)
+        for (int v = 0; v < V; ++v) {
           interior(Ar::from(xa.v[v]), Ar::from(xb.v[v]), Ar::from(xc.v[v]), Ar::from(xd.v[v]));
+          if constexpr (R > K) {  // chunk spans several checkpoint intervals
+            if ((r + v + 1) % K == 0 && r + v + 1 < R) checkpoint(row0 + r + v);
+          }
+        }
       }
     } else {
 #pragma unroll 1
@@ -348,6 +363,9 @@ __global__ void __launch_bounds__(W * 32)
             a0 = av; b0 = bv; c0 = cv; d0 = dv;
           } else if (row < L - 1) {
             interior(av, bv, cv, dv);
+            if constexpr (R > K) {
+              if ((row + 1) % K == 0 && r + 1 < R) checkpoint(row);
+            }
           } else {
             const T ratio = Ar::mul_nn(av, rbp);
             beta = Ar::sub_mul_dom(bv, ratio, cprev);
@@ -359,14 +377,9 @@ __global__ void __launch_bounds__(W * 32)
       }
     }
     renorm();
-    // checkpoint after every K rows, when the next K rows start with an
-    // interior row (Stage 3 restarts its K-row chunk there)
-    if (active && ((row0 + R) % K) == 0 && row0 + R <= L - 2) {
-      const int64_t slot = (int64_t)((row0 + R) / K - 1) * lv.p + k;
-      Ar::to(ck_gam[slot], Ar::mul(cprev, rbp));
-      Ar::to(ck_y[slot], Ar::mul(g, rbp));
-      Ar::to(ck_v[slot], Ar::mul(al, rbp));
-    }
+    // the checkpoint at the chunk's end (row0 + R is a multiple of K when
+    // K divides R, and every K / R chunks otherwise)
+    if (((row0 + R) % K) == 0) checkpoint(row0 + R - 1);
     __syncwarp();  // the buffer is refilled by the next iteration's copies
   }
   if (active) {

@@ -88,14 +88,17 @@ static cudaError_t set_smem(K kernel, size_t smem, bool& done) {
   return e;
 }
 
-// Stage 1 streams half-size chunks (more warps fit in shared memory) and
-// writes a checkpoint every K rows, K being Stage 3's chunk length.
+// Stage 1 streams chunks of K rows (or a multiple) and writes a checkpoint
+// every K rows, K being Stage 3's chunk length.
+#ifndef TPS_STAGE1_MUL
+#define TPS_STAGE1_MUL 1  // Stage-1 chunk rows = K * TPS_STAGE1_MUL (measured best: 1)
+#endif
 template <class Ar, class Tin, class Tred, int K>
 static cudaError_t launch_stage1(const Level& lv, const Tin* a, const Tin* b, const Tin* c,
                                  const Tin* d, Tred* ra, Tred* rb, Tred* rc, Tred* rd, Tred* cg,
                                  Tred* cy, Tred* cv, int* status, cudaStream_t s) {
   constexpr int W = kWarpsPerCta;
-  constexpr int R = K / 2;
+  constexpr int R = K * TPS_STAGE1_MUL;
   const size_t smem = Tile<Tin, R>::kBytesPerWarp * W;
   const int64_t warps = (lv.k_end - lv.k_begin + 31) / 32;
   const unsigned grid = (unsigned)((warps + W - 1) / W);
@@ -151,7 +154,7 @@ static cudaError_t run_levels(tps_plan_s* P, const std::vector<LevelPlan>& level
     return cudaGetLastError();
   }
   const LevelPlan& L = levels[idx];
-  constexpr int R = sizeof(Tin) >= 8 ? 8 : 16;
+  constexpr int R = kChunkRows<Tin>;
   Tred* red[5];
   for (int i = 0; i < 5; ++i) red[i] = reinterpret_cast<Tred*>(P->ws + L.off_red[i]);
   Tred* ck[3];
@@ -187,7 +190,7 @@ cudaError_t stage1_range(tps_plan_s* P, const LevelPlan& L, int64_t kb, int64_t 
     using Ar = decltype(ar);
     using Tin = std::remove_pointer_t<decltype(tin)>;
     using Tred = std::remove_pointer_t<decltype(tred)>;
-    constexpr int R = sizeof(Tin) >= 8 ? 8 : 16;
+    constexpr int R = kChunkRows<Tin>;
     Level lv = L.lv;
     lv.k_begin = kb;
     lv.k_end = ke;
@@ -208,7 +211,7 @@ cudaError_t stage3_range(tps_plan_s* P, const LevelPlan& L, int64_t kb, int64_t 
     using Ar = decltype(ar);
     using Tin = std::remove_pointer_t<decltype(tin)>;
     using Tred = std::remove_pointer_t<decltype(tred)>;
-    constexpr int R = sizeof(Tin) >= 8 ? 8 : 16;
+    constexpr int R = kChunkRows<Tin>;
     Level lv = L.lv;
     lv.k_begin = kb;
     lv.k_end = ke;

@@ -16,8 +16,16 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 // Rows per shared-memory chunk (and checkpoint spacing) for an element size.
-inline int chunk_rows(size_t elem_bytes) { return elem_bytes >= 8 ? 8 : 16; }
-constexpr int kWarpsPerCta = 1;
+#ifndef TPS_CHUNK_ROWS_8B
+#define TPS_CHUNK_ROWS_8B 8  // Stage-3 chunk rows (checkpoint spacing) for 8-byte elements
+#endif
+inline int chunk_rows(size_t elem_bytes) { return elem_bytes >= 8 ? TPS_CHUNK_ROWS_8B : 16; }
+template <class T>
+constexpr int kChunkRows = sizeof(T) >= 8 ? TPS_CHUNK_ROWS_8B : 16;
+#ifndef TPS_WARPS_PER_CTA
+#define TPS_WARPS_PER_CTA 1
+#endif
+constexpr int kWarpsPerCta = TPS_WARPS_PER_CTA;
 
 // One level of the recursive solve: the system at this level has lv.n rows
 // and is split into lv.p blocks; its reduced system (2 lv.p rows) and the
