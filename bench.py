@@ -14,6 +14,8 @@ Stage 2, Stage 3).
            kernels and D2H on the plan's streams, all inside the timed region;
            link_floor_ms is the same bytes moved as plain copies (H2D, then
            D2H) in the same run, the bound no pipeline can beat
+           (e2e.zero_copy: the same through TPS_ZERO_COPY, kernels reading
+           and writing pinned, and pageable, host memory directly)
   batched  4096 packed systems, n_i log-uniform in [2^8, 2^20] (--no-extra
            skips this and the next)
   mixed    the refinement workload (b = 1.01 (|a| + |c|)) in every arithmetic
@@ -218,6 +220,33 @@ def time_device(plan, g, x, steps, warmup, world, stream):
     ms = e0.elapsed_time(e1) / steps
     info = plan.query()
     return max_over_ranks(ms, world), info
+
+
+def time_host(plan, hk, hx, stream, steps, warmup, world):
+    """(first call ms, mean ms per step) of tps_solve_host_async on host
+    buffers; the first call also pays any first-touch mapping cost."""
+    import torch
+
+    def once():
+        plan.solve_host_async(hk["a"], hk["b"], hk["c"], hk["d"], hx, stream=stream)
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    once()
+    e1.record(stream)
+    stream.synchronize()
+    first = e0.elapsed_time(e1)
+    for _ in range(max(warmup - 1, 0)):
+        once()
+    stream.synchronize()
+    barrier(world)
+    e0.record(stream)
+    for _ in range(steps):
+        once()
+    e1.record(stream)
+    stream.synchronize()
+    barrier(world)
+    return first, max_over_ranks(e0.elapsed_time(e1) / steps, world)
 
 
 def link_floor(hk, hx, g, x, stream, reps=3):
@@ -432,7 +461,25 @@ def main():
         infoh = plan_h.query()
         eh_err = (hx.to("cuda") - g["x_true"]).abs().max().item() / g["x_true"].abs().max().item()
         floor_ms = link_floor(hk, hx, g, x, stream)
-        del hk, hx, plan_h
+        del plan_h
+        # zero copy: kernels on host memory, pinned and pageable
+        zc = {}
+        if not a.no_extra:
+            plan_z = binding.Plan(n, dtype="f64_df", residency="host", m=a.m,
+                                  m_reduced=a.m_reduced, flags=binding.ZERO_COPY | binding.GRAPH)
+            kinds = [("pinned", hk, hx)]
+            if plan_z.query()["pageable_ok"]:
+                kinds.append(("pageable", {k: g[k].cpu() for k in "abcd"},
+                              torch.empty(n, dtype=torch.float64)))
+            for kind, hin, hout in kinds:
+                first, zms = time_host(plan_z, hin, hout, stream, esteps, min(a.warmup, 3), world)
+                zerr = ((hout.to("cuda") - g["x_true"]).abs().max().item()
+                        / g["x_true"].abs().max().item())
+                zc[kind] = {"value": world * n / (zms * 1e-3), "unit": UNIT, "ms_per_step": zms,
+                            "first_call_ms": first, "frac_of_link_floor": floor_ms / zms,
+                            "rel_fwd_vs_x_true": zerr}
+            del plan_z, kinds
+        del hk, hx
         extra = {}
         if not a.no_extra:
             extra = extra_workloads(binding, synth, world, rank, stream, a)
@@ -472,7 +519,7 @@ def main():
                 "steps": esteps, "h2d_bytes_per_step": 4 * 8 * n, "d2h_bytes_per_step": 8 * n,
                 "streams": infoh["streams"], "chunk": infoh["chunk"],
                 "link_floor_ms": floor_ms, "frac_of_link_floor": floor_ms / ems,
-                "rel_fwd_vs_x_true": eh_err},
+                "rel_fwd_vs_x_true": eh_err, "zero_copy": zc},
         "clocks": clocks,
     }
     line.update(extra)

@@ -72,6 +72,8 @@ typedef enum {
 #define TPS_TRACE 4u              /* record per-stage event times (tps_plan_query) */
 #define TPS_EXTERNAL_WORKSPACE 8u /* caller supplies the workspace                */
 #define TPS_GRAPH 16u             /* replay Stage 2 as one CUDA graph launch      */
+#define TPS_ZERO_COPY 32u         /* host residency: kernels, not copy engines,   */
+                                  /* move host data (see tps_solve_host_async)    */
 
 typedef struct {
   int64_t n_max;     /* largest n of tps_solve / tps_solve_host_async, or the  */
@@ -85,7 +87,8 @@ typedef struct {
   int32_t max_iters; /* refinement iteration cap; 0 = 10                       */
   int64_t chunk;     /* rows per host-pipeline chunk; 0 = choose               */
   double tol;        /* refinement stop: ||delta||/||x|| <= tol; 0 = 1e-12     */
-  uint32_t flags;    /* TPS_TUNE_* | TPS_TRACE | TPS_EXTERNAL_WORKSPACE        */
+  uint32_t flags;    /* TPS_TUNE_* | TPS_TRACE | TPS_EXTERNAL_WORKSPACE |      */
+                     /* TPS_GRAPH | TPS_ZERO_COPY                              */
   uint32_t reserved; /* must be 0                                              */
 } tps_plan_desc;
 
@@ -102,6 +105,9 @@ typedef struct {
   double last_correction; /* ||delta||/||x|| of the last refinement step          */
   float stage_ms[4];     /* TPS_TRACE: stage 1, stage 2, stage 3, total (last solve) */
   size_t workspace_bytes;
+  int32_t pageable_ok;   /* TPS_ZERO_COPY plans: 1 if pageable host memory is     */
+                         /* accepted (the device reads it coherently), else 0     */
+  int32_t reserved;
 } tps_info;
 
 /* Create a plan.  Validates `desc` (n_max >= 0, dtype, m 0 or >= 2, streams
@@ -155,7 +161,18 @@ tps_status tps_solve_batched(tps_plan_t plan, int64_t count, const int64_t* offs
  * a, b, c, d between the stages, so nothing is uploaded twice.  Work is
  * ordered after everything already in `stream`, and `stream` waits for all
  * of it; the call returns after enqueueing.  Pageable memory gives
- * TPS_ERR_INVALID_ARG. */
+ * TPS_ERR_INVALID_ARG.
+ *
+ * With TPS_ZERO_COPY no copy engine is used: the same chunked pipeline moves
+ * each chunk with a streaming kernel whose threads load from and store to
+ * host memory directly (consecutive threads, consecutive 16-byte vectors),
+ * concurrent with the stage kernels of other chunks.  The link carries the
+ * same bytes (each input once up, x once down).  Host arrays may then be
+ * pinned memory, or ordinary pageable memory where the device has coherent
+ * access to it (cudaDevAttrPageableMemoryAccess, e.g. Grace-based systems;
+ * tps_plan_query reports it); elsewhere pageable memory gives
+ * TPS_ERR_INVALID_ARG.  The pages must stay mapped until `stream`
+ * completes.  mixed dtype: TPS_ERR_UNSUPPORTED. */
 tps_status tps_solve_host_async(tps_plan_t plan, int64_t n, const void* a, const void* b,
                                 const void* c, const void* d, void* x, void* stream);
 

@@ -18,7 +18,7 @@ STATUS = {0: "TPS_OK", 1: "TPS_ERR_INVALID_ARG", 2: "TPS_ERR_UNSUPPORTED", 3: "T
           7: "TPS_ERR_TIMEOUT"}
 DTYPES = {"f64": 0, "f32": 1, "mixed": 2, "f64_df": 3}
 RESIDENCY = {"device": 0, "host": 1}
-TUNE_PREDICT, TUNE_EXHAUSTIVE, TRACE, EXTERNAL_WORKSPACE, GRAPH = 1, 2, 4, 8, 16
+TUNE_PREDICT, TUNE_EXHAUSTIVE, TRACE, EXTERNAL_WORKSPACE, GRAPH, ZERO_COPY = 1, 2, 4, 8, 16, 32
 
 # every symbol include/tps.h declares
 EXPORTS = ("tps_plan", "tps_plan_destroy", "tps_workspace_size", "tps_set_workspace", "tps_solve",
@@ -40,7 +40,8 @@ class Info(ctypes.Structure):
                 ("m", ctypes.c_int32), ("m_reduced", ctypes.c_int32),
                 ("streams", ctypes.c_int32), ("levels", ctypes.c_int32),
                 ("chunk", ctypes.c_int64), ("last_correction", ctypes.c_double),
-                ("stage_ms", ctypes.c_float * 4), ("workspace_bytes", ctypes.c_size_t)]
+                ("stage_ms", ctypes.c_float * 4), ("workspace_bytes", ctypes.c_size_t),
+                ("pageable_ok", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class TpsError(RuntimeError):
@@ -154,7 +155,8 @@ class Plan:
         return x
 
     def solve_host_async(self, a, b, c, d, x, stream=None):
-        """a..x are pinned CPU tensors; returns after enqueueing."""
+        """a..x are pinned CPU tensors (ZERO_COPY plans: or pageable ones where
+        the device reads pageable memory); returns after enqueueing."""
         n = b.numel()
         check(lib().tps_solve_host_async(self._h, n, _ptr(a), _ptr(b), _ptr(c), _ptr(d),
                                          _ptr(x), _stream(stream)), "tps_solve_host_async")
@@ -167,7 +169,8 @@ class Plan:
                 "iterations": info.iterations, "m": info.m, "m_reduced": info.m_reduced,
                 "streams": info.streams, "levels": info.levels, "chunk": info.chunk,
                 "last_correction": info.last_correction,
-                "stage_ms": list(info.stage_ms), "workspace_bytes": info.workspace_bytes}
+                "stage_ms": list(info.stage_ms), "workspace_bytes": info.workspace_bytes,
+                "pageable_ok": bool(info.pageable_ok)}
 
 
 def status_string(s):

@@ -3,6 +3,7 @@
 // then Stage 3 back up the levels.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <type_traits>
 #include <vector>
 
@@ -167,6 +168,46 @@ static cudaError_t run_levels(tps_plan_s* P, const std::vector<LevelPlan>& level
   if (e != cudaSuccess) return e;
   return launch_stage3<Ar, Tin, Tred, R>(L.lv, a, b, c, d, red[4], ck[0], ck[1], ck[2], x,
                                          P->d_status, s);
+}
+
+// ------------------------------------------------------------------ kernel copies
+// Grid-stride copy in 16-byte vectors (both pointers 16-byte aligned) or
+// 4-byte words; consecutive threads move consecutive vectors, so every warp
+// instruction covers 512 contiguous bytes of both sides.
+__global__ void k_copy16(const float4* __restrict__ src, float4* __restrict__ dst, size_t n16,
+                         const uint32_t* __restrict__ src_tail, uint32_t* __restrict__ dst_tail,
+                         int tail_words) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n16; i += stride)
+    dst[i] = src[i];
+  if (blockIdx.x == 0 && (int)threadIdx.x < tail_words) dst_tail[threadIdx.x] = src_tail[threadIdx.x];
+}
+__global__ void k_copy4(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, size_t n4) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += stride)
+    dst[i] = src[i];
+}
+
+cudaError_t kernel_copy(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return cudaSuccess;
+  if ((bytes | (uintptr_t)dst | (uintptr_t)src) % 4) return cudaErrorInvalidValue;
+  constexpr int kThreads = 256;
+  constexpr size_t kMaxBlocks = 152 * 4;  // four CTAs per SM saturate the host link
+  if (((uintptr_t)dst | (uintptr_t)src) % 16 == 0) {
+    const size_t n16 = bytes / 16;
+    const int tail = (int)((bytes % 16) / 4);
+    const size_t blocks = std::max<size_t>(1, std::min(kMaxBlocks, (n16 + kThreads - 1) / kThreads));
+    k_copy16<<<(unsigned)blocks, kThreads, 0, s>>>(
+        static_cast<const float4*>(src), static_cast<float4*>(dst), n16,
+        reinterpret_cast<const uint32_t*>(static_cast<const unsigned char*>(src) + n16 * 16),
+        reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(dst) + n16 * 16), tail);
+  } else {
+    const size_t n4 = bytes / 4;
+    const size_t blocks = std::max<size_t>(1, std::min(kMaxBlocks, (n4 + kThreads - 1) / kThreads));
+    k_copy4<<<(unsigned)blocks, kThreads, 0, s>>>(static_cast<const uint32_t*>(src),
+                                                  static_cast<uint32_t*>(dst), n4);
+  }
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ dtype dispatch

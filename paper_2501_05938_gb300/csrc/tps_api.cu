@@ -110,8 +110,9 @@ tps_status tps_plan(const tps_plan_desc* desc, tps_plan_t* out) {
   if (d.streams != 0 && (d.streams < 1 || d.streams > 32)) return TPS_ERR_INVALID_ARG;
   if (d.chunk < 0 || d.max_iters < 0 || d.tol < 0.0) return TPS_ERR_INVALID_ARG;
   if (d.flags & ~(TPS_TUNE_PREDICT | TPS_TUNE_EXHAUSTIVE | TPS_TRACE | TPS_EXTERNAL_WORKSPACE |
-                  TPS_GRAPH))
+                  TPS_GRAPH | TPS_ZERO_COPY))
     return TPS_ERR_INVALID_ARG;
+  if ((d.flags & TPS_ZERO_COPY) && d.residency != TPS_HOST_PINNED) return TPS_ERR_INVALID_ARG;
 
   tps_plan_s* P = new (std::nothrow) tps_plan_s();
   if (!P) return TPS_ERR_OOM;
@@ -149,6 +150,13 @@ tps_status tps_plan(const tps_plan_desc* desc, tps_plan_t* out) {
   }
   P->off_levels = off_levels;
 
+  if (d.flags & TPS_ZERO_COPY) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrPageableMemoryAccess, dev) == cudaSuccess)
+      P->pageable_ok = v != 0;
+    cudaGetLastError();
+  }
   if (d.residency == TPS_HOST_PINNED) {
     HostPipe* H = new (std::nothrow) HostPipe();
     if (!H) { delete P; return TPS_ERR_OOM; }
@@ -271,14 +279,16 @@ static bool device_ptr_ok(const void* p, size_t align) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-static bool host_pinned_ok(const void* p, size_t align) {
+// Host pointer check: pinned host memory, or (pageable_ok: the device has
+// coherent access to pageable memory) memory no CUDA allocator owns.
+static bool host_ptr_ok(const void* p, size_t align, bool pageable_ok) {
   if (!p || ((uintptr_t)p % align) != 0) return false;
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeHost;
+  return at.type == cudaMemoryTypeHost || (pageable_ok && at.type == cudaMemoryTypeUnregistered);
 }
 
 static bool overlaps(const void* x, const void* y, size_t bytes) {
@@ -294,11 +304,12 @@ static tps_status check_solve_args(tps_plan_s* P, int64_t n, const void* a, cons
   if (n == 0) return TPS_OK;
   const size_t es = elem_bytes_io(P->desc.dtype);
   const void* in[4] = {a, b, c, d};
+  const bool pageable = host && (P->desc.flags & TPS_ZERO_COPY) && P->pageable_ok;
   for (const void* p : in) {
-    if (host ? !host_pinned_ok(p, es) : !device_ptr_ok(p, es)) return TPS_ERR_INVALID_ARG;
+    if (host ? !host_ptr_ok(p, es, pageable) : !device_ptr_ok(p, es)) return TPS_ERR_INVALID_ARG;
     if (overlaps(p, x, (size_t)n * es)) return TPS_ERR_INVALID_ARG;
   }
-  if (host ? !host_pinned_ok(x, es) : !device_ptr_ok(x, es)) return TPS_ERR_INVALID_ARG;
+  if (host ? !host_ptr_ok(x, es, pageable) : !device_ptr_ok(x, es)) return TPS_ERR_INVALID_ARG;
   return TPS_OK;
 }
 
@@ -377,6 +388,13 @@ tps_status tps_solve_host_async(tps_plan_t P, int64_t n, const void* a, const vo
   const size_t span = align_up((size_t)P->desc.n_max * es);
   unsigned char* dev[5];
   for (int i = 0; i < 5; ++i) dev[i] = P->ws + H->off_dev + i * span;
+  // TPS_ZERO_COPY: a streaming kernel moves each chunk (SM loads and stores
+  // on host memory) instead of the copy engines
+  const bool zc = (P->desc.flags & TPS_ZERO_COPY) != 0;
+  auto copy = [&](void* dst, const void* src, size_t bytes, cudaMemcpyKind kind,
+                  cudaStream_t s) -> cudaError_t {
+    return zc ? kernel_copy(dst, src, bytes, s) : cudaMemcpyAsync(dst, src, bytes, kind, s);
+  };
   const unsigned char* host[5] = {(const unsigned char*)a, (const unsigned char*)b,
                                   (const unsigned char*)c, (const unsigned char*)d,
                                   (const unsigned char*)x};
@@ -391,10 +409,10 @@ tps_status tps_solve_host_async(tps_plan_t P, int64_t n, const void* a, const vo
   if (lv.empty()) {  // small system: one stream, one chunk
     cudaStream_t s0 = H->streams[0];
     for (int i = 0; i < 4 && e == cudaSuccess; ++i)
-      e = cudaMemcpyAsync(dev[i], host[i], (size_t)n * es, cudaMemcpyHostToDevice, s0);
+      e = copy(dev[i], host[i], (size_t)n * es, cudaMemcpyHostToDevice, s0);
     if (e == cudaSuccess) e = base_solve(P, n, dev[0], dev[1], dev[2], dev[3], dev[4], s0);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync((void*)host[4], dev[4], (size_t)n * es, cudaMemcpyDeviceToHost, s0);
+      e = copy((void*)host[4], dev[4], (size_t)n * es, cudaMemcpyDeviceToHost, s0);
     if (e == cudaSuccess) e = cudaEventRecord(H->ev_done3[0], s0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(us, H->ev_done3[0], 0);
     P->last_stream = us;
@@ -419,8 +437,8 @@ tps_status tps_solve_host_async(tps_plan_t P, int64_t n, const void* a, const vo
     int64_t kb, ke, r0, r1;
     chunk_rows(j, kb, ke, r0, r1);
     for (int i = 0; i < 4 && e == cudaSuccess; ++i)
-      e = cudaMemcpyAsync(dev[i] + r0 * es, host[i] + r0 * es, (size_t)(r1 - r0) * es,
-                          cudaMemcpyHostToDevice, s);
+      e = copy(dev[i] + r0 * es, host[i] + r0 * es, (size_t)(r1 - r0) * es,
+               cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = stage1_range(P, lv[0], kb, ke, dev[0], dev[1], dev[2], dev[3], s);
   }
   // join, Stage 2 on stream 0, fork
@@ -440,8 +458,8 @@ tps_status tps_solve_host_async(tps_plan_t P, int64_t n, const void* a, const vo
     chunk_rows(j, kb, ke, r0, r1);
     e = stage3_range(P, lv[0], kb, ke, dev[0], dev[1], dev[2], dev[3], dev[4], s);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync((void*)(host[4] + r0 * es), dev[4] + r0 * es, (size_t)(r1 - r0) * es,
-                          cudaMemcpyDeviceToHost, s);
+      e = copy((void*)(host[4] + r0 * es), dev[4] + r0 * es, (size_t)(r1 - r0) * es,
+               cudaMemcpyDeviceToHost, s);
   }
   for (int i = 0; i < S && e == cudaSuccess; ++i) {
     e = cudaEventRecord(H->ev_done3[i], H->streams[i]);
@@ -512,6 +530,7 @@ tps_status tps_plan_query(tps_plan_t P, tps_info* out) {
   out->iterations = P->last_iters;
   out->last_correction = P->last_corr;
   out->workspace_bytes = P->ws_needed;
+  out->pageable_ok = (P->desc.flags & TPS_ZERO_COPY) && P->pageable_ok ? 1 : 0;
   for (int i = 0; i < 4; ++i) out->stage_ms[i] = P->stage_ms[i];
   if (!P->ws) return TPS_OK;
   cudaStream_t s = P->last_stream;

@@ -79,6 +79,8 @@ struct tps_plan_s {
   cudaGraphExec_t graph = nullptr;
   cudaStream_t cap_stream = nullptr;
   int64_t gkey[12] = {};
+  // TPS_ZERO_COPY: the device can read and write pageable host memory
+  bool pageable_ok = false;
   // batched work list (device) and its capacity in entries
   void* d_work = nullptr;
   size_t work_cap = 0;
@@ -106,6 +108,10 @@ cudaError_t stage3_range(tps_plan_s* P, const LevelPlan& L, int64_t kb, int64_t 
                          const void* a, const void* b, const void* c, const void* d, void* x,
                          cudaStream_t s);
 cudaError_t reduced_solve(tps_plan_s* P, const std::vector<LevelPlan>& levels, cudaStream_t s);
+// Copy `bytes` between host and device memory with a streaming kernel (SM
+// loads and stores, no copy engine); either side may be host memory the
+// device can address.  bytes and both pointers: multiples of 4.
+cudaError_t kernel_copy(void* dst, const void* src, size_t bytes, cudaStream_t s);
 // The same, captured once into a CUDA graph (TPS_GRAPH) and replayed.
 cudaError_t reduced_solve_graph(tps_plan_s* P, const std::vector<LevelPlan>& levels,
                                 cudaStream_t s);

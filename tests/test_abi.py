@@ -48,7 +48,7 @@ def test_status_strings_and_version(lib):
 @pytest.mark.parametrize("field,value", [("n_max", -1), ("dtype", 7), ("residency", 3), ("m", 1),
                                          ("m_reduced", 2), ("streams", 33), ("streams", -1),
                                          ("chunk", -5), ("reserved", 1), ("flags", 1 << 10),
-                                         ("tol", -1.0)])
+                                         ("tol", -1.0), ("flags", 32)])
 def test_plan_rejects_bad_descriptors_on_the_host(lib, field, value):
     d = binding.PlanDesc(n_max=1000, dtype=0)
     setattr(d, field, value)

@@ -214,6 +214,46 @@ def test_host_pipeline_rejects_pageable_and_device_memory():
                                                        x.pin_memory())
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f64_df", "f32"])
+@pytest.mark.parametrize("mem", ["pinned", "pageable"])
+@pytest.mark.parametrize("n,m", [(50, 32), (100003, 32), (262145, 128), (65536 * 3 + 1, 64)])
+def test_zero_copy_matches_oracle(dtype, mem, n, m):
+    """TPS_ZERO_COPY: Stage 1 reads host memory directly and mirrors it,
+    Stage 3 writes x straight to host memory."""
+    s = synth.system(7000 + n, n)
+    tdt = torch.float64
+    if dtype == "f32":
+        s, tdt = synth.to_f32(s), torch.float32
+    plan = binding.Plan(n, dtype=dtype, residency="host", m=m, flags=binding.ZERO_COPY)
+    if mem == "pageable" and not plan.query()["pageable_ok"]:
+        pytest.skip("the device has no coherent access to pageable host memory")
+    host = [torch.as_tensor(np.ascontiguousarray(s[k])).to(tdt) for k in "abcd"]
+    x = torch.full((n,), float("nan"), dtype=tdt)
+    if mem == "pinned":
+        host, x = [t.pin_memory() for t in host], x.pin_memory()
+    stream = torch.cuda.Stream()
+    plan.solve_host_async(*host, x, stream=stream)
+    stream.synchronize()
+    assert plan.query()["status"] == 0
+    a, b, c, d = (np.asarray(s[k], dtype=np.float64) for k in "abcd")
+    ref = oracle.thomas(a, b, c, d)
+    xs = x.numpy().astype(np.float64)
+    fwd, res = (F32_FWD, F32_RES) if dtype == "f32" else (F64_FWD, F64_RES)
+    assert oracle.rel_forward_error(xs, ref) <= fwd
+    assert oracle.rel_residual(a, b, c, d, xs) <= res
+
+
+def test_zero_copy_needs_host_residency_and_host_memory():
+    n = 1000
+    with pytest.raises(binding.TpsError):
+        binding.Plan(n, dtype="f64", flags=binding.ZERO_COPY)  # device residency
+    plan = binding.Plan(n, dtype="f64", residency="host", flags=binding.ZERO_COPY)
+    s = synth.system(2, n)
+    dv = [torch.as_tensor(s[k]).cuda() for k in "abcd"]
+    with pytest.raises(binding.TpsError):
+        plan.solve_host_async(*dv, torch.empty(n, dtype=torch.float64, device="cuda"))
+
+
 def test_trace_reports_stage_times():
     n = 1 << 20
     g = synth.system_device(9, n)
