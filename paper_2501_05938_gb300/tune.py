@@ -12,8 +12,12 @@
            3 * 2^k sizes, an unseen batch count) for the MLP, for the paper's
            stream rule (Eq. 4, 6, 7) refit on this GPU's timings, and for the
            fixed defaults
+  paper    the paper's own modelling pipeline on this GPU's host-pipeline
+           timings: sum model, both overhead models, their R-squared / MSE /
+           RMSE on a shuffled 3:1 split, and the rule's stream counts against
+           the measured optimum per size; writes paper_models_gb300.json
 
-Usage: python -m paper_2501_05938_gb300.tune collect|train|evaluate|all [dir]
+Usage: python -m paper_2501_05938_gb300.tune collect|train|evaluate|paper|all [dir]
 """
 from __future__ import annotations
 
@@ -362,10 +366,14 @@ def paper_rule_coeffs(rows):
 
 
 def paper_rule_streams(n, coeffs):
+    """The rule of Eq. 6 with the models of Eq. 4 and Eq. 7, evaluated in
+    libtps; coeffs None: the paper's RTX 2080 Ti coefficients."""
     L = binding.lib()
     L.tps_paper_predict_streams.argtypes = [ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_double]
     L.tps_paper_predict_streams.restype = ctypes.c_int32
+    if coeffs is None:
+        return int(L.tps_paper_predict_streams(float(n), None, None, None, 1e6))
     s, sm, bg = (np.ascontiguousarray(c, dtype=np.float64) for c in coeffs)
     return int(L.tps_paper_predict_streams(float(n), s.ctypes.data, sm.ctypes.data,
                                            bg.ctypes.data, 1e6))
@@ -413,6 +421,97 @@ def evaluate(rows, weights_path):
     return summary, detail, coeffs
 
 
+# ---------------------------------------------------------------------------
+# the paper's modelling pipeline (Sec. 2.4, Tables 4 and 6) on this GPU
+# ---------------------------------------------------------------------------
+SPLIT_SEED = 2025
+
+
+def _split(count, seed):
+    """Shuffled 3:1 train/test split of `count` samples (indices)."""
+    perm = np.random.RandomState(seed).permutation(count)
+    cut = (3 * count + 3) // 4
+    return perm[:cut], perm[cut:]
+
+
+def _metrics(y, yhat):
+    y, yhat = np.asarray(y, float), np.asarray(yhat, float)
+    mse = float(np.mean((y - yhat) ** 2))
+    tot = float(np.sum((y - y.mean()) ** 2))
+    r2 = 1.0 - float(np.sum((y - yhat) ** 2)) / tot if tot > 0 else 0.0
+    return {"r2": r2, "mse": mse, "rmse": math.sqrt(mse), "samples": int(len(y))}
+
+
+def _lsq(cols, y):
+    return np.linalg.lstsq(np.stack(cols, axis=1), np.asarray(y, float), rcond=None)[0]
+
+
+def paper_samples(rows, dtype=0):
+    """Per size: the overlapped sum (Eq. 3: the Stage-1 and Stage-3 kernel
+    time; the reduced transfers of the paper's CPU Stage 2 do not exist
+    here), T_non_str (one stream, one chunk) and T_str(S) (S streams, one
+    chunk per stream), from the host-pipeline sweep."""
+    sums = {r["n"]: r["s13_ms"] for r in rows
+            if r["kind"] == "device" and r["m"] == M_HOST and r["dtype"] == dtype}
+    t = {}
+    for r in rows:
+        if r["kind"] == "host" and r["dtype"] == dtype and r["chunk"] == 0 and r["n"] in sums:
+            t.setdefault(r["n"], {})[r["S"]] = r["ms"]
+    return {n: {"sum": sums[n], "t": t[n]} for n in sorted(t) if 1 in t[n]}
+
+
+def paper_models(rows, dtype=0, seed=SPLIT_SEED, split=1e6):
+    """Eq. 4 (linear sum model) and the two Eq. 7 forms (T_overhead of Eq. 5,
+    small for size <= 1e6, big above) fitted on a shuffled 3:1 split, their
+    R-squared / MSE / RMSE on both sets, and the rule of Eq. 6 with the
+    fitted models against the measured optimum stream count per size.  The
+    preset forms are linear in their coefficients, so least squares gives
+    the coefficients a curve fit converges to."""
+    smp = paper_samples(rows, dtype)
+    ns = np.array(sorted(smp), float)
+    sums = np.array([smp[int(n)]["sum"] for n in ns])
+    tr, te = _split(len(ns), seed)
+    k, q = _lsq([ns[tr], np.ones(len(tr))], sums[tr])
+    sum_fit = {"coeffs": [float(k), float(q)],
+               "train": _metrics(sums[tr], k * ns[tr] + q),
+               "test": _metrics(sums[te], k * ns[te] + q)}
+    # Eq. 5 per (size, S > 1), with the measured sum
+    ov = {"small": [], "big": []}
+    for n in sorted(smp):
+        t1, sm = smp[n]["t"][1], smp[n]["sum"]
+        for S, ts in sorted(smp[n]["t"].items()):
+            if S > 1:
+                ov["small" if n <= split else "big"].append(
+                    (float(n), float(S), (ts - t1) + (S - 1) / S * sm))
+    forms = {
+        "small": lambda n, S: [n, np.log10(S), np.ones_like(n)],
+        "big": lambda n, S: [n * (4.0 / 3.0) * np.log2(S), (4.0 / 3.0) * np.log2(S),
+                             np.ones_like(n)],
+    }
+    ov_fit = {}
+    for name, pts in ov.items():
+        a = np.array(pts, float)
+        tr2, te2 = _split(len(a), seed + (1 if name == "big" else 0))
+        co = _lsq(forms[name](a[tr2, 0], a[tr2, 1]), a[tr2, 2])
+        pred = lambda idx: np.stack(forms[name](a[idx, 0], a[idx, 1]), axis=1) @ co
+        ov_fit[name] = {"coeffs": [float(c) for c in co], "train": _metrics(a[tr2, 2], pred(tr2)),
+                        "test": _metrics(a[te2, 2], pred(te2))}
+    coeffs = (np.array(sum_fit["coeffs"]), np.array(ov_fit["small"]["coeffs"]),
+              np.array(ov_fit["big"]["coeffs"]))
+    table = []
+    for n in sorted(smp):
+        t = smp[n]["t"]
+        act = min(t, key=t.get)
+        pre = paper_rule_streams(n, coeffs)
+        pre_2080 = paper_rule_streams(n, None)
+        table.append({"n": n, "N_act": act, "N_pre": pre, "N_pre_2080ti": pre_2080,
+                      "T1_ms": t[1], "T_act_ms": t[act], "T_pre_ms": t.get(pre, float("nan")),
+                      "speedup_act": t[1] / t[act], "regret_pre": t.get(pre, float("nan")) / t[act] - 1,
+                      "regret_pre_2080ti": t.get(pre_2080, float("nan")) / t[act] - 1})
+    return {"dtype": dtype, "seed": seed, "split": split, "sum_model": sum_fit,
+            "overhead_small": ov_fit["small"], "overhead_big": ov_fit["big"], "table": table}
+
+
 def main(argv):
     cmd = argv[1] if len(argv) > 1 else "all"
     out = argv[2] if len(argv) > 2 else PRED_DIR
@@ -432,6 +531,15 @@ def main(argv):
             json.dump({"summary": summary, "detail": detail,
                        "paper_rule_coeffs": [list(map(float, c)) for c in coeffs]}, f, indent=1)
         print(json.dumps(summary))
+    if cmd in ("paper", "all"):
+        res = paper_models(rows)
+        with open(os.path.join(out, "paper_models_gb300.json"), "w") as f:
+            json.dump(res, f, indent=1)
+        for k in ("sum_model", "overhead_small", "overhead_big"):
+            print(k, json.dumps({s: res[k][s] for s in ("coeffs", "train", "test")}))
+        for r in res["table"]:
+            print(r["n"], r["N_act"], r["N_pre"], r["N_pre_2080ti"], round(r["speedup_act"], 3),
+                  round(r["regret_pre"], 4))
 
 
 if __name__ == "__main__":
