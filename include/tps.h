@@ -74,6 +74,7 @@ typedef enum {
 #define TPS_GRAPH 16u             /* replay Stage 2 as one CUDA graph launch      */
 #define TPS_ZERO_COPY 32u         /* host residency: kernels, not copy engines,   */
                                   /* move host data (see tps_solve_host_async)    */
+#define TPS_NO_ONCHIP 64u         /* never use the single-launch on-chip solve    */
 
 typedef struct {
   int64_t n_max;     /* largest n of tps_solve / tps_solve_host_async, or the  */
@@ -88,7 +89,7 @@ typedef struct {
   int64_t chunk;     /* rows per host-pipeline chunk; 0 = choose               */
   double tol;        /* refinement stop: ||delta||/||x|| <= tol; 0 = 1e-12     */
   uint32_t flags;    /* TPS_TUNE_* | TPS_TRACE | TPS_EXTERNAL_WORKSPACE |      */
-                     /* TPS_GRAPH | TPS_ZERO_COPY                              */
+                     /* TPS_GRAPH | TPS_ZERO_COPY | TPS_NO_ONCHIP              */
   uint32_t reserved; /* must be 0                                              */
 } tps_plan_desc;
 
@@ -100,14 +101,16 @@ typedef struct {
   int32_t m;             /* parameters the plan uses                              */
   int32_t m_reduced;
   int32_t streams;
-  int32_t levels;        /* partition levels of the last solve                    */
+  int32_t levels;        /* partition levels of the last solve launched level by  */
+                         /* level (those before an on-chip solve)                 */
   int64_t chunk;
   double last_correction; /* ||delta||/||x|| of the last refinement step          */
   float stage_ms[4];     /* TPS_TRACE: stage 1, stage 2, stage 3, total (last solve) */
   size_t workspace_bytes;
   int32_t pageable_ok;   /* TPS_ZERO_COPY plans: 1 if pageable host memory is     */
                          /* accepted (the device reads it coherently), else 0     */
-  int32_t reserved;
+  int32_t onchip;        /* last solve: 0 all levels by separate launches; 1 the   */
+                         /* whole system, 2 its reduced system, solved on chip     */
 } tps_info;
 
 /* Create a plan.  Validates `desc` (n_max >= 0, dtype, m 0 or >= 2, streams
@@ -139,7 +142,18 @@ tps_status tps_set_workspace(tps_plan_t plan, void* dev_ptr, size_t bytes);
  * system, a chain of small launches that touches only the workspace -- into
  * a CUDA graph on a private stream at the first solve with a given level
  * geometry, and replays it as one graph launch afterwards (also from
- * tps_solve_batched and the host pipeline). */
+ * tps_solve_batched and the host pipeline).
+ *
+ * A system that fits in the GPU's shared memory (up to ~0.89 M rows in
+ * fp64 and double-float, ~1.8 M in fp32 on 152 SMs; not for packed batches)
+ * is solved by a single cooperative launch that reads a, b, c, d once and
+ * writes x once: each CTA eliminates its rows on chip, one grid barrier,
+ * every CTA solves the small system of CTA interface rows, and recovers its
+ * rows on chip.  The reduced system of a larger solve takes the same path
+ * once it fits.  TPS_NO_ONCHIP keeps every level on separate launches.
+ * The barrier waits a bounded time; if it runs out (which needs CTAs that
+ * are not co-resident) the solve stops and tps_plan_query reports
+ * TPS_ERR_TIMEOUT. */
 tps_status tps_solve(tps_plan_t plan, int64_t n, const void* a, const void* b, const void* c,
                      const void* d, void* x, void* stream);
 

@@ -18,7 +18,8 @@ STATUS = {0: "TPS_OK", 1: "TPS_ERR_INVALID_ARG", 2: "TPS_ERR_UNSUPPORTED", 3: "T
           7: "TPS_ERR_TIMEOUT"}
 DTYPES = {"f64": 0, "f32": 1, "mixed": 2, "f64_df": 3}
 RESIDENCY = {"device": 0, "host": 1}
-TUNE_PREDICT, TUNE_EXHAUSTIVE, TRACE, EXTERNAL_WORKSPACE, GRAPH, ZERO_COPY = 1, 2, 4, 8, 16, 32
+TUNE_PREDICT, TUNE_EXHAUSTIVE, TRACE, EXTERNAL_WORKSPACE, GRAPH, ZERO_COPY, NO_ONCHIP = (
+    1, 2, 4, 8, 16, 32, 64)
 
 # every symbol include/tps.h declares
 EXPORTS = ("tps_plan", "tps_plan_destroy", "tps_workspace_size", "tps_set_workspace", "tps_solve",
@@ -41,7 +42,7 @@ class Info(ctypes.Structure):
                 ("streams", ctypes.c_int32), ("levels", ctypes.c_int32),
                 ("chunk", ctypes.c_int64), ("last_correction", ctypes.c_double),
                 ("stage_ms", ctypes.c_float * 4), ("workspace_bytes", ctypes.c_size_t),
-                ("pageable_ok", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("pageable_ok", ctypes.c_int32), ("onchip", ctypes.c_int32)]
 
 
 class TpsError(RuntimeError):
@@ -170,7 +171,7 @@ class Plan:
                 "streams": info.streams, "levels": info.levels, "chunk": info.chunk,
                 "last_correction": info.last_correction,
                 "stage_ms": list(info.stage_ms), "workspace_bytes": info.workspace_bytes,
-                "pageable_ok": bool(info.pageable_ok)}
+                "pageable_ok": bool(info.pageable_ok), "onchip": info.onchip}
 
 
 def status_string(s):

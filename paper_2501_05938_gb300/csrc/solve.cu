@@ -1,15 +1,104 @@
 // Recursive device-resident partition solve: Stage 1 on the input, the same
-// method on the reduced interface system (Stage 2) until it fits one warp,
-// then Stage 3 back up the levels.
+// method on the reduced interface system (Stage 2) until it fits one warp
+// or the GPU's shared memory (the single-launch on-chip solve), then Stage 3
+// back up the levels.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <type_traits>
 #include <vector>
 
+#include "onchip.cuh"
 #include "tps_internal.h"
 
 namespace tps {
+
+size_t onchip_exchange_bytes() { return (size_t)4 * 2 * kOcMaxCtas * 8; }
+
+// ------------------------------------------------------------------ on-chip solve
+struct OcGeom {
+  int mt;     // level-0 block rows (odd)
+  int64_t p;  // level-0 blocks
+  int G;      // CTAs
+};
+
+// The smallest odd block length (>= 3) whose CTA count fits `ctas_max`;
+// a one-row tail is merged into the block before it.
+template <class Tin>
+static bool oc_geometry(int64_t n, int ctas_max, OcGeom& g) {
+  if (n <= kBaseMax) return false;
+  for (int mt = 3; mt <= oc_mt_max<Tin>(); mt += 2) {
+    int64_t p = (n + mt - 1) / mt;
+    if (n - (p - 1) * mt == 1) --p;
+    const int64_t G = (p + kOcThreads - 1) / kOcThreads;
+    if (G <= ctas_max) {
+      g = {mt, p, (int)G};
+      return true;
+    }
+  }
+  return false;
+}
+
+// CTAs of k_onchip<Ar, Tin> that can be resident at once on the current
+// device (at most kOcMaxCtas), found once per device; 0 if it cannot run.
+template <class Ar, class Tin>
+static int oc_ctas_max() {
+  static int cache[16] = {};
+  static bool have[16] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (!have[dev]) {
+    int sms = 0, per = 0;
+    const size_t smem = OcLayout<Ar, Tin>::kBytes;
+    if (cudaFuncSetAttribute(k_onchip<Ar, Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_onchip<Ar, Tin>, kOcThreads,
+                                                      smem) != cudaSuccess) {
+      cudaGetLastError();
+      per = 0;
+    }
+    cache[dev] = std::min(kOcMaxCtas, sms * per);
+    have[dev] = true;
+  }
+  return cache[dev];
+}
+
+// Solve the system on chip if it fits (used = true), else leave it.
+template <class Ar, class Tin>
+static cudaError_t launch_onchip(tps_plan_s* P, int64_t n, const Tin* a, const Tin* b,
+                                 const Tin* c, const Tin* d, Tin* x, cudaStream_t s,
+                                 bool& used) {
+  used = false;
+  if (P->desc.flags & TPS_NO_ONCHIP) return cudaSuccess;
+  OcGeom g;
+  if (!oc_geometry<Tin>(n, oc_ctas_max<Ar, Tin>(), g)) return cudaSuccess;
+  unsigned* bar = reinterpret_cast<unsigned*>(P->ws + 32);
+  using T = typename Ar::T;
+  T* xch = reinterpret_cast<T*>(P->ws + P->off_xch);
+  const uintptr_t al = (uintptr_t)a | (uintptr_t)b | (uintptr_t)c | (uintptr_t)d | (uintptr_t)x;
+  const int vec16 = (al % 16) == 0;
+  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)g.G);
+  cfg.blockDim = dim3(kOcThreads);
+  cfg.dynamicSmemBytes = OcLayout<Ar, Tin>::kBytes;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const unsigned arrivals = (unsigned)g.G + (P->test_barrier_extra ? 1u : 0u);
+  e = cudaLaunchKernelEx(&cfg, k_onchip<Ar, Tin>, n, g.mt, g.p, a, b, c, d, x, xch, bar,
+                         arrivals, P->d_status, vec16);
+  if (e == cudaSuccess) used = true;
+  return e;
+}
 
 Level make_level(int64_t n, int m, int R) {
   Level lv{};
@@ -153,6 +242,15 @@ static cudaError_t run_levels(tps_plan_s* P, const std::vector<LevelPlan>& level
     if (n <= 0) return cudaSuccess;
     k_base<Ar, Tin, Tin><<<1, 32, 0, s>>>(n, a, b, c, d, x, nullptr, 0, P->d_status);
     return cudaGetLastError();
+  }
+  bool used = false;
+  cudaError_t eo = launch_onchip<Ar, Tin>(P, n, a, b, c, d, x, s, used);
+  if (eo != cudaSuccess || used) {
+    if (used) {
+      P->last_onchip = 2;
+      P->last_levels = (int32_t)idx;  // levels launched before the on-chip solve
+    }
+    return eo;
   }
   const LevelPlan& L = levels[idx];
   constexpr int R = kChunkRows<Tin>;
@@ -328,7 +426,11 @@ cudaError_t reduced_solve_graph(tps_plan_s* P, const std::vector<LevelPlan>& lev
       return e;
     }
     for (int i = 0; i < 12; ++i) P->gkey[i] = key[i];
+    P->graph_onchip = P->last_onchip;
+    P->graph_levels = P->last_levels;
   }
+  P->last_onchip = P->graph_onchip;
+  P->last_levels = P->graph_levels;
   return cudaGraphLaunch(P->graph, s);
 }
 
@@ -336,8 +438,25 @@ tps_status run_solve(tps_plan_s* P, int64_t n, const void* a, const void* b, con
                      const void* d, void* x, cudaStream_t s, const std::vector<LevelPlan>& lv,
                      cudaEvent_t* ev, const int64_t* bnd, int64_t nbnd) {
   cudaError_t e = cudaSuccess;
+  P->last_onchip = 0;
   if (ev) e = cudaEventRecord(ev[0], s);
-  if (lv.empty()) {
+  bool onchip = false;
+  if (e == cudaSuccess && !lv.empty() && nbnd == 0) {  // the whole system on chip
+    e = dispatch(P->desc.dtype, [&](auto ar, auto* tin, auto* tred) -> cudaError_t {
+      using Ar = decltype(ar);
+      using Tin = std::remove_pointer_t<decltype(tin)>;
+      (void)tred;
+      return launch_onchip<Ar, Tin>(P, n, (const Tin*)a, (const Tin*)b, (const Tin*)c,
+                                    (const Tin*)d, (Tin*)x, s, onchip);
+    });
+    if (onchip) {
+      P->last_onchip = 1;
+      P->last_levels = 0;
+    }
+  }
+  if (onchip) {
+    for (int i = 1; i < 3 && e == cudaSuccess && ev; ++i) e = cudaEventRecord(ev[i], s);
+  } else if (lv.empty()) {
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
     if (e == cudaSuccess) e = base_solve(P, n, a, b, c, d, x, s, bnd, nbnd);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);

@@ -54,7 +54,9 @@ static void default_params(const tps_plan_desc& d, int32_t& m, int32_t& mr, int3
 
 static size_t workspace_for(tps_plan_s* P, size_t* off_levels_out, size_t* off_dev_out) {
   size_t off = 0;
-  off = align_up(off + 64);  // status word and refinement maxima
+  off = align_up(off + 64);  // status word, refinement maxima, grid-barrier counter
+  P->off_xch = off;          // interface rows of the on-chip solve
+  off = align_up(off + onchip_exchange_bytes());
   *off_levels_out = off;
   std::vector<LevelPlan> lv;
   const size_t eio = elem_bytes_io(P->desc.dtype);
@@ -110,7 +112,7 @@ tps_status tps_plan(const tps_plan_desc* desc, tps_plan_t* out) {
   if (d.streams != 0 && (d.streams < 1 || d.streams > 32)) return TPS_ERR_INVALID_ARG;
   if (d.chunk < 0 || d.max_iters < 0 || d.tol < 0.0) return TPS_ERR_INVALID_ARG;
   if (d.flags & ~(TPS_TUNE_PREDICT | TPS_TUNE_EXHAUSTIVE | TPS_TRACE | TPS_EXTERNAL_WORKSPACE |
-                  TPS_GRAPH | TPS_ZERO_COPY))
+                  TPS_GRAPH | TPS_ZERO_COPY | TPS_NO_ONCHIP))
     return TPS_ERR_INVALID_ARG;
   if ((d.flags & TPS_ZERO_COPY) && d.residency != TPS_HOST_PINNED) return TPS_ERR_INVALID_ARG;
 
@@ -150,6 +152,8 @@ tps_status tps_plan(const tps_plan_desc* desc, tps_plan_t* out) {
   }
   P->off_levels = off_levels;
 
+  if (const char* t = std::getenv("TPS_TEST_ONCHIP_TIMEOUT"))
+    P->test_barrier_extra = t[0] == '1';
   if (d.flags & TPS_ZERO_COPY) {
     int dev = 0, v = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
@@ -531,6 +535,7 @@ tps_status tps_plan_query(tps_plan_t P, tps_info* out) {
   out->last_correction = P->last_corr;
   out->workspace_bytes = P->ws_needed;
   out->pageable_ok = (P->desc.flags & TPS_ZERO_COPY) && P->pageable_ok ? 1 : 0;
+  out->onchip = P->last_onchip;
   for (int i = 0; i < 4; ++i) out->stage_ms[i] = P->stage_ms[i];
   if (!P->ws) return TPS_OK;
   cudaStream_t s = P->last_stream;

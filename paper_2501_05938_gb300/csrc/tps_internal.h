@@ -81,6 +81,16 @@ struct tps_plan_s {
   int64_t gkey[12] = {};
   // TPS_ZERO_COPY: the device can read and write pageable host memory
   bool pageable_ok = false;
+  // on-chip solve: exchange rows for the CTAs' interface equations, and
+  // which part of the last solve ran on chip (0 none, 1 all, 2 reduced)
+  size_t off_xch = 0;
+  int32_t last_onchip = 0;
+  int32_t graph_onchip = 0;  // last_onchip and last_levels of the captured Stage 2
+  int32_t graph_levels = 0;
+  // test hook (TPS_TEST_ONCHIP_TIMEOUT=1 at plan creation): the on-chip
+  // solve's grid barrier waits for one CTA more than it launches, so the
+  // bounded wait runs out and the solve reports TPS_ERR_TIMEOUT
+  bool test_barrier_extra = false;
   // batched work list (device) and its capacity in entries
   void* d_work = nullptr;
   size_t work_cap = 0;
@@ -108,6 +118,8 @@ cudaError_t stage3_range(tps_plan_s* P, const LevelPlan& L, int64_t kb, int64_t 
                          const void* a, const void* b, const void* c, const void* d, void* x,
                          cudaStream_t s);
 cudaError_t reduced_solve(tps_plan_s* P, const std::vector<LevelPlan>& levels, cudaStream_t s);
+// Bytes of the on-chip solve's exchange rows (part of every plan workspace).
+size_t onchip_exchange_bytes();
 // Copy `bytes` between host and device memory with a streaming kernel (SM
 // loads and stores, no copy engine); either side may be host memory the
 // device can address.  bytes and both pointers: multiples of 4.

@@ -52,13 +52,20 @@ CASES = [(1, 32), (2, 32), (3, 2), (63, 8), (64, 32), (65, 32), (65, 2), (100, 3
          (1 << 20, 32), ((1 << 20) + 7, 100)]
 
 
+@pytest.mark.parametrize("onchip", [True, False])
 @pytest.mark.parametrize("dtype", ["f64", "f64_df"])
 @pytest.mark.parametrize("n,m", CASES)
-def test_fp64_paths_match_oracle(dtype, n, m):
+def test_fp64_paths_match_oracle(dtype, n, m, onchip):
+    """Both routes: the single-launch on-chip solve where the system fits,
+    and the multi-launch levels (TPS_NO_ONCHIP)."""
     s = synth.system(1000 + n, n)
-    plan = binding.Plan(n, dtype=dtype, m=m)
+    plan = binding.Plan(n, dtype=dtype, m=m, flags=0 if onchip else binding.NO_ONCHIP)
     x, info = run(plan, s)
     assert info["status"] == 0
+    if not onchip:
+        assert info["onchip"] == 0
+    elif n > 64:
+        assert info["onchip"] in (1, 2)
     ref = oracle.thomas(s["a"], s["b"], s["c"], s["d"])
     fwd = oracle.rel_forward_error(x, ref)
     res = oracle.rel_residual(s["a"], s["b"], s["c"], s["d"], x)
@@ -70,9 +77,11 @@ def test_fp64_paths_match_oracle(dtype, n, m):
 
 @pytest.mark.parametrize("n,m,mr", [(1 << 16, 256, 4), (1 << 18, 2, 8), (50000, 1000, 1000)])
 def test_reduced_block_sizes(n, m, mr):
+    """Unusual block sizes on the level-by-level route (the on-chip solve
+    would take these sizes whole)."""
     s = synth.system(5 + n, n)
     for dtype in ("f64", "f64_df"):
-        plan = binding.Plan(n, dtype=dtype, m=m, m_reduced=mr)
+        plan = binding.Plan(n, dtype=dtype, m=m, m_reduced=mr, flags=binding.NO_ONCHIP)
         x, info = run(plan, s)
         ref = oracle.thomas(s["a"], s["b"], s["c"], s["d"])
         assert oracle.rel_forward_error(x, ref) <= F64_FWD
