@@ -19,6 +19,8 @@ Stage 2, Stage 3).
   batched  4096 packed systems, n_i log-uniform in [2^8, 2^20] (--no-extra
            skips this and the next)
   mixed    the refinement workload (b = 1.01 (|a| + |c|)) in every arithmetic
+  midsize_f64_df  n = 65536 and 800000: the single-launch on-chip solve
+           against the level-by-level route (L2-warm)
   roofline the dominant kernel's algorithmic bytes over its mean duration
            (CUDA events recorded by the library on the launch stream during
            the timed steps) against the measured HBM copy bandwidth
@@ -405,6 +407,34 @@ def extra_workloads(binding, synth, world, rank, stream, a):
         del plan
     out["mixed"] = mres
     del g, x
+    # mid-size single systems: the single-launch on-chip solve against the
+    # level-by-level route (inputs fit in L2, so these are L2-warm times)
+    mid = {}
+    for n in (65536, 800000):
+        g = synth.system_device(1006 + rank, n)
+        x = torch.empty_like(g["b"])
+        row = {}
+        for name, fl in (("onchip", binding.GRAPH), ("levels", binding.GRAPH | binding.NO_ONCHIP)):
+            plan = binding.Plan(n, dtype="f64_df", flags=fl)
+            for _ in range(3):
+                plan.solve(g["a"], g["b"], g["c"], g["d"], x, stream=stream)
+            stream.synchronize()
+            steps = 50
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                plan.solve(g["a"], g["b"], g["c"], g["d"], x, stream=stream)
+            e1.record(stream)
+            stream.synchronize()
+            us = max_over_ranks(e0.elapsed_time(e1) / steps, world) * 1e3
+            q = plan.query()
+            err = ((x - g["x_true"]).abs().max() / g["x_true"].abs().max()).item()
+            row[name] = {"us_per_solve": us, "value": world * n / (us * 1e-6), "launches": 2 * q["levels"] + 1,
+                         "onchip": q["onchip"], "rel_fwd_vs_x_true": err}
+        row["speedup"] = row["levels"]["us_per_solve"] / row["onchip"]["us_per_solve"]
+        mid[str(n)] = row
+        del g, x
+    out["midsize_f64_df"] = mid
     return out
 
 
