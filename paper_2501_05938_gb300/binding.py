@@ -163,6 +163,24 @@ class Plan:
                                          _ptr(x), _stream(stream)), "tps_solve_host_async")
         return x
 
+    def autotune(self, a, b, c, d, x, reps=3, offsets=None, host_offsets=None, stream=None):
+        """tps_autotune: time every block size on these arrays and keep the
+        fastest in the plan (plans made with TUNE_EXHAUSTIVE cover the whole
+        grid); returns (m, ms per solve)."""
+        L = lib()
+        P = ctypes.c_void_p
+        L.tps_autotune.argtypes = [P, ctypes.c_int64, ctypes.c_int64, P, P, P, P, P, P, P, P,
+                                   ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                   ctypes.POINTER(ctypes.c_float)]
+        L.tps_autotune.restype = ctypes.c_int
+        m, ms = ctypes.c_int32(), ctypes.c_float()
+        count = 0 if offsets is None else offsets.numel() - 1
+        hp = None if host_offsets is None else ctypes.c_void_p(host_offsets.ctypes.data)
+        check(L.tps_autotune(self._h, b.numel(), count, _ptr(offsets), hp, _ptr(a), _ptr(b),
+                             _ptr(c), _ptr(d), _ptr(x), _stream(stream), int(reps),
+                             ctypes.byref(m), ctypes.byref(ms)), "tps_autotune")
+        return m.value, ms.value
+
     def query(self):
         info = Info()
         check(lib().tps_plan_query(self._h, ctypes.byref(info)), "tps_plan_query")

@@ -123,7 +123,9 @@ int tps_predict_params(const tps_plan_desc* desc, int32_t* m, int32_t* streams,
   *streams = 1 << clamp_pow2(y[1] * w->oscale[1], 0, 5);
   const int lc = clamp_pow2(y[2] * w->oscale[2], 10, 40);
   int64_t c = (int64_t)1 << lc;
-  if (c > (int64_t)n) c = 0;  // one chunk per stream
+  // one chunk per stream when the chunk exceeds n; and on a single stream
+  // chunks run back to back with nothing to overlap, so none at all
+  if (c > (int64_t)n || *streams == 1) c = 0;
   *chunk = c;
   return 0;
 }

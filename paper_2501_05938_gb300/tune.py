@@ -112,7 +112,8 @@ def collect(path, log=print):
             a, b, c, d = (dev[dt][k][:n] for k in "abcd")
             x = xs[dt][:n]
             for m in M_GRID:
-                plan = binding.Plan(n, dtype=dt, m=m, m_reduced=32, flags=binding.TRACE)
+                plan = binding.Plan(n, dtype=dt, m=m, m_reduced=32,
+                                    flags=binding.TRACE | binding.GRAPH)
                 ms = _time(lambda: plan.solve(a, b, c, d, x, stream=stream), stream)
                 st = plan.query()["stage_ms"]
                 rows.append(dict(kind="device", n=n, batch=1, dtype=DTYPES[dt], residency=0,
@@ -132,7 +133,8 @@ def collect(path, log=print):
             x = torch.empty(n, dtype=tdt, device="cuda")
             offs = torch.as_tensor(off, device="cuda")
             for m in M_GRID:
-                plan = binding.Plan(n, dtype=dt, m=m, m_reduced=32, batch_max=batch)
+                plan = binding.Plan(n, dtype=dt, m=m, m_reduced=32, batch_max=batch,
+                                    flags=binding.GRAPH)
                 ms = _time(lambda: plan.solve_batched(offs, a, b, c, d, x, host_offsets=off,
                                                       stream=stream), stream)
                 rows.append(dict(kind="batched", n=n, batch=batch, dtype=DTYPES[dt],
@@ -380,6 +382,7 @@ def paper_rule_streams(n, coeffs):
 
 
 def default_params(n, residency):
+    """The library's defaults (tps_plan with zero parameters, no predictor)."""
     m = 128
     while m > 8 and n // m < 152 * 32 * 4:
         m //= 2
