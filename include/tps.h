@@ -75,6 +75,7 @@ typedef enum {
 #define TPS_ZERO_COPY 32u         /* host residency: kernels, not copy engines,   */
                                   /* move host data (see tps_solve_host_async)    */
 #define TPS_NO_ONCHIP 64u         /* never use the single-launch on-chip solve    */
+#define TPS_TRUNCATE 128u         /* approximate windowed solve (see tps_solve)   */
 
 typedef struct {
   int64_t n_max;     /* largest n of tps_solve / tps_solve_host_async, or the  */
@@ -89,7 +90,8 @@ typedef struct {
   int64_t chunk;     /* rows per host-pipeline chunk; 0 = choose               */
   double tol;        /* refinement stop: ||delta||/||x|| <= tol; 0 = 1e-12     */
   uint32_t flags;    /* TPS_TUNE_* | TPS_TRACE | TPS_EXTERNAL_WORKSPACE |      */
-                     /* TPS_GRAPH | TPS_ZERO_COPY | TPS_NO_ONCHIP              */
+                     /* TPS_GRAPH | TPS_ZERO_COPY | TPS_NO_ONCHIP |            */
+                     /* TPS_TRUNCATE                                           */
   uint32_t reserved; /* must be 0                                              */
 } tps_plan_desc;
 
@@ -151,6 +153,19 @@ tps_status tps_set_workspace(tps_plan_t plan, void* dev_ptr, size_t bytes);
  * every CTA solves the small system of CTA interface rows, and recovers its
  * rows on chip.  The reduced system of a larger solve takes the same path
  * once it fits.  TPS_NO_ONCHIP keeps every level on separate launches.
+ *
+ * TPS_TRUNCATE (device plans, fp64 / double-float / fp32; not the paper's
+ * method, an approximation for strongly dominant systems): windows of m kept
+ * rows are solved independently, each on chip as the system on the window
+ * plus m_reduced halo rows on either side with the couplings beyond cut; one
+ * pass over the arrays, no reduced system.  m (even) and m_reduced (even)
+ * must satisfy m + 2 m_reduced <= 1792; 0 chooses (the halo for the plan's
+ * tol at a dominance factor max(|a|+|c|)/|b| of 3/4, the window from the
+ * rest).  Each window bounds its own error from its dominance factor q and
+ * smallest |b|: (|a_cut| q^h + |c_cut| q^h) / ((1 - q) min|b|) relative to
+ * max|x|; tps_plan_query reports the largest bound of the last solve in
+ * last_correction and TPS_ERR_NO_CONVERGENCE if it exceeds tol (default
+ * 1e-12).
  * The barrier waits a bounded time; if it runs out (which needs CTAs that
  * are not co-resident) the solve stops and tps_plan_query reports
  * TPS_ERR_TIMEOUT. */

@@ -20,6 +20,7 @@ DTYPES = {"f64": 0, "f32": 1, "mixed": 2, "f64_df": 3}
 RESIDENCY = {"device": 0, "host": 1}
 TUNE_PREDICT, TUNE_EXHAUSTIVE, TRACE, EXTERNAL_WORKSPACE, GRAPH, ZERO_COPY, NO_ONCHIP = (
     1, 2, 4, 8, 16, 32, 64)
+TRUNCATE = 128
 
 # every symbol include/tps.h declares
 EXPORTS = ("tps_plan", "tps_plan_destroy", "tps_workspace_size", "tps_set_workspace", "tps_solve",

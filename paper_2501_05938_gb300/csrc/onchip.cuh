@@ -156,6 +156,63 @@ __device__ __forceinline__ void oc_bwd(const Acc& A, int L, typename Ar::T f,
   A.set_x(0, f);
 }
 
+// The intra-CTA levels of a CTA whose level-1 system (N rows, starting at
+// level row 0) sits in lv: Stage 1 in kOcBlock-row blocks until at most
+// kOcFinal rows are left, recording each level's offset and size; on return
+// `off` and `N` describe the last level (one block).  Needs every thread.
+struct OcLevels {
+  int off = 0, N = 0, nl = 0;
+  int offs[4], Ns[4];  // at most 3 levels: 512 -> 128 -> 32 -> 8 rows
+};
+template <class Ar>
+__device__ __forceinline__ void oc_reduce_levels(typename Ar::T* const* lv, int N1, int tid,
+                                                 OcLevels& L, bool& bad) {
+  using T = typename Ar::T;
+  T red[8];
+  L.off = 0;
+  L.N = N1;
+  L.nl = 0;
+  while (L.N > kOcFinal) {
+    const int pl = (L.N + kOcBlock - 1) / kOcBlock;
+    const int noff = L.off + L.N;
+    if (tid < pl) {
+      const int len = tid == pl - 1 ? L.N - kOcBlock * (pl - 1) : kOcBlock;
+      const AccLv<Ar> A{{lv[0], lv[1], lv[2], lv[3]}, L.off + kOcBlock * tid};
+      oc_fwd<Ar>(A, len, red, bad);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        lv[q][lvx(noff + 2 * tid)] = red[q];
+        lv[q][lvx(noff + 2 * tid + 1)] = red[4 + q];
+      }
+    }
+    __syncthreads();
+    L.offs[L.nl] = L.off;
+    L.Ns[L.nl] = L.N;
+    ++L.nl;
+    L.off = noff;
+    L.N = 2 * pl;
+  }
+}
+
+// Stage 3 back down the levels recorded by oc_reduce_levels, given the last
+// level's solution in its d slots; leaves level 1's solution in lv[3].
+template <class Ar>
+__device__ __forceinline__ void oc_expand_levels(typename Ar::T* const* lv, int tid,
+                                                 const OcLevels& L) {
+  using T = typename Ar::T;
+  for (int li = L.nl - 1; li >= 0; --li) {
+    const int Nl = L.Ns[li], ol = L.offs[li], pl = (Nl + kOcBlock - 1) / kOcBlock;
+    const int onext = ol + Nl;
+    if (tid < pl) {
+      const int len = tid == pl - 1 ? Nl - kOcBlock * (pl - 1) : kOcBlock;
+      const T fl = lv[3][lvx(onext + 2 * tid)], ll = lv[3][lvx(onext + 2 * tid + 1)];
+      const AccLv<Ar> A{{lv[0], lv[1], lv[2], lv[3]}, ol + kOcBlock * tid};
+      oc_bwd<Ar>(A, len, fl, ll);
+    }
+    __syncthreads();
+  }
+}
+
 // a value of 4 or 8 bytes read from L2, past the (non-coherent) L1
 template <class T>
 __device__ __forceinline__ T ld_l2(const T* p) {
@@ -243,28 +300,9 @@ __global__ void __launch_bounds__(kOcThreads, 1)
   __syncthreads();
 
   // ---- Stage 1, levels 1..: 8-row blocks until one block is left
-  int N = 2 * nb, off = 0, nl = 0;
-  int offs[4], Ns[4];  // at most 3 levels: 512 -> 128 -> 32 -> 8 rows
-  while (N > kOcFinal) {
-    const int pl = (N + kOcBlock - 1) / kOcBlock;
-    const int noff = off + N;
-    if (tid < pl) {
-      const int L = tid == pl - 1 ? N - kOcBlock * (pl - 1) : kOcBlock;
-      const AccLv<Ar> A{{lv[0], lv[1], lv[2], lv[3]}, off + kOcBlock * tid};
-      oc_fwd<Ar>(A, L, red, bad);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        lv[q][lvx(noff + 2 * tid)] = red[q];
-        lv[q][lvx(noff + 2 * tid + 1)] = red[4 + q];
-      }
-    }
-    __syncthreads();
-    offs[nl] = off;
-    Ns[nl] = N;
-    ++nl;
-    off = noff;
-    N = 2 * pl;
-  }
+  OcLevels lev;
+  oc_reduce_levels<Ar>(lv, 2 * nb, tid, lev, bad);
+  const int off = lev.off, N = lev.N;
   // the CTA's own two interface equations
   const int M = 2 * G;
   if (tid == 0) {
@@ -351,17 +389,7 @@ __global__ void __launch_bounds__(kOcThreads, 1)
     oc_bwd<Ar>(A, N, fc, lc);
   }
   __syncthreads();
-  for (int li = nl - 1; li >= 0; --li) {
-    const int Nl = Ns[li], ol = offs[li], pl = (Nl + kOcBlock - 1) / kOcBlock;
-    const int onext = ol + Nl;
-    if (tid < pl) {
-      const int L = tid == pl - 1 ? Nl - kOcBlock * (pl - 1) : kOcBlock;
-      const T fl = lv[3][lvx(onext + 2 * tid)], ll = lv[3][lvx(onext + 2 * tid + 1)];
-      const AccLv<Ar> A{{lv[0], lv[1], lv[2], lv[3]}, ol + kOcBlock * tid};
-      oc_bwd<Ar>(A, L, fl, ll);
-    }
-    __syncthreads();
-  }
+  oc_expand_levels<Ar>(lv, tid, lev);
   if (tid < nb) {
     const int64_t k = kb + tid;
     const T fl = lv[3][lvx(2 * tid)], ll = lv[3][lvx(2 * tid + 1)];
@@ -374,6 +402,175 @@ __global__ void __launch_bounds__(kOcThreads, 1)
   for (int i = tid; i < nv; i += kOcThreads)
     *reinterpret_cast<float4*>(x + r0 + i * V) = *reinterpret_cast<const float4*>(s0[3] + i * V);
   for (int i = nv * V + tid; i < rows; i += kOcThreads) x[r0 + i] = s0[3][i];
+}
+
+}  // namespace tps
+
+namespace tps {
+
+// ------------------------------------------------------------------ truncated decoupling
+// Not the paper's method: an approximation for strongly dominant systems
+// (TPS_TRUNCATE).  Window w keeps rows [wR, wR + R) and is solved, on chip
+// in one CTA, as the tridiagonal system on the extended rows
+// [wR - h, wR + R + h) (clipped to [0, n)) with the couplings that leave that
+// range cut.  With q = max (|a| + |c|) / |b| over the window (cut couplings
+// zero) the inverse of the window's matrix decays like q^|i-j|, so the kept
+// rows differ from the exact solution by at most
+//     (|a_cut| q^dl + |c_cut| q^dr) / ((1 - q) min |b|) * ||x||_inf,
+// dl, dr the distances from the kept rows to the two cut ends.  Each window
+// publishes that bound (maximum over windows, as the bits of a
+// non-negative float) and flags ST_NO_CONVERGENCE where it exceeds `tol`.
+constexpr int kWinThreads = 128;
+constexpr int kWinRowsMax = 1792;              // extended rows of one window
+constexpr int kWinLevelRows = 256 + 64 + 16 + 4;
+constexpr int kWinLevelSlots = kWinLevelRows + kWinLevelRows / kOcBlock + kOcBlock;
+
+// Shared memory of a window of at most `rows` extended rows: the level
+// arrays first (fixed size), then four row arrays of `rows` elements.
+template <class Ar, class Tin>
+struct WinLayout {
+  using T = typename Ar::T;
+  static constexpr size_t kLv = ((size_t)kWinLevelSlots * sizeof(T) + 15) / 16 * 16;
+  __host__ __device__ static constexpr size_t l0(int rows) {
+    return ((size_t)rows * sizeof(Tin) + 15) / 16 * 16;
+  }
+  __host__ __device__ static constexpr size_t bytes(int rows) { return 4 * (kLv + l0(rows)); }
+};
+
+__device__ __forceinline__ float abs_f(double v) { return (float)fabs(v); }
+__device__ __forceinline__ float abs_f(float v) { return fabsf(v); }
+__device__ __forceinline__ float abs_f(float2 v) { return fabsf(v.x); }
+
+// R, h even; one CTA per window.
+template <class Ar, class Tin>
+__global__ void __launch_bounds__(kWinThreads)
+    k_window(int64_t n, int R, int h, const Tin* __restrict__ a, const Tin* __restrict__ b,
+             const Tin* __restrict__ c, const Tin* __restrict__ d, Tin* __restrict__ x, float tol,
+             unsigned* __restrict__ bound_max, int* __restrict__ status, int vec16) {
+  using T = typename Ar::T;
+  using Lay = WinLayout<Ar, Tin>;
+  static_assert(sizeof(T) <= sizeof(Tin), "relations are stored in the input slots");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Tin* s0[4];
+  T* lv[4];
+  const size_t l0 = Lay::l0(R + 2 * h);
+  for (int k = 0; k < 4; ++k) {
+    lv[k] = reinterpret_cast<T*>(smem_raw + k * Lay::kLv);
+    s0[k] = reinterpret_cast<Tin*>(smem_raw + 4 * Lay::kLv + k * l0);
+  }
+  __shared__ unsigned q_bits, bmin_bits;
+  __shared__ float cut_s[2];
+  const int tid = (int)threadIdx.x;
+  const int64_t k0 = (int64_t)blockIdx.x * R;
+  const int64_t k1 = k0 + R < n ? k0 + R : n;
+  const int64_t e0 = k0 - h > 0 ? k0 - h : 0;
+  const int64_t e1 = k1 + h < n ? k1 + h : n;
+  const int E = (int)(e1 - e0);
+
+  // ---- load the extended rows (16-byte pieces only where the window start
+  // is a whole number of pieces from the 16-byte aligned base)
+  const Tin* const src[4] = {a, b, c, d};
+  constexpr int V = 16 / (int)sizeof(Tin);
+  const int nv = (vec16 && e0 % V == 0) ? E / V : 0;
+  for (int k = 0; k < 4; ++k) {
+    for (int i = tid; i < nv; i += kWinThreads) cp_async<16>(s0[k] + i * V, src[k] + e0 + i * V);
+    for (int i = nv * V + tid; i < E; i += kWinThreads)
+      cp_async<sizeof(Tin)>(s0[k] + i, src[k] + e0 + i);
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();  // every thread's copies have landed
+  if (tid == 0) {
+    cut_s[0] = e0 > 0 ? abs_f(s0[0][0]) : 0.0f;  // the couplings being cut
+    cut_s[1] = e1 < n ? abs_f(s0[2][E - 1]) : 0.0f;
+    q_bits = 0u;
+    bmin_bits = 0x7f800000u;  // +inf
+    s0[0][0] = Tin{};
+    s0[2][E - 1] = Tin{};
+  }
+  __syncthreads();
+  // ---- q and min |b| of the window (cut couplings zero), rounded up / down
+  float qmax = 0.0f, bmin = __int_as_float(0x7f800000);
+  for (int i = tid; i < E; i += kWinThreads) {
+    const float bb = abs_f(s0[1][i]);
+    const float qq = __fdiv_ru(__fadd_ru(abs_f(s0[0][i]), abs_f(s0[2][i])), bb);
+    qmax = fmaxf(qmax, qq);
+    bmin = fminf(bmin, bb);
+  }
+  // |b| from hi parts and fp32 rounding: widen q by a relative 2^-20 margin
+  qmax = __fmul_ru(qmax, 1.0f + 9.5367431640625e-07f);
+  bmin = __fmul_rd(bmin, 1.0f - 9.5367431640625e-07f);
+  atomicMax(&q_bits, __float_as_uint(qmax));
+  atomicMin(&bmin_bits, __float_as_uint(bmin));
+  __syncthreads();  // every row read before Stage 1 overwrites a, b, c in place
+
+  // ---- Stage 1: thread blocks of mt rows (odd) over the E rows, then levels
+  int mt = (E + kWinThreads - 1) / kWinThreads;
+  if (mt < 3) mt = 3;
+  mt |= 1;
+  int p = (E + mt - 1) / mt;
+  if (p > 1 && E - (p - 1) * mt == 1) --p;  // merge a one-row tail
+  bool bad = false;
+  T red[8];
+  const int myL = tid < p ? (tid == p - 1 ? E - tid * mt : mt) : 0;
+  if (tid < p) {
+    const AccL0<Ar, Tin> A{{s0[0], s0[1], s0[2], s0[3]}, tid * mt};
+    oc_fwd<Ar>(A, myL, red, bad);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      lv[q][lvx(2 * tid)] = red[q];
+      lv[q][lvx(2 * tid + 1)] = red[4 + q];
+    }
+  }
+  __syncthreads();
+  OcLevels lev;
+  oc_reduce_levels<Ar>(lv, 2 * p, tid, lev, bad);
+  // ---- the window's two interface equations, with nothing outside: a 2x2 system
+  if (tid == 0) {
+    const AccLv<Ar> A{{lv[0], lv[1], lv[2], lv[3]}, lev.off};
+    oc_fwd<Ar>(A, lev.N, red, bad);
+    // b1 f + c1 l = d1;  a2 f + b2 l = d2
+    const T det = Ar::sub_mul(Ar::mul(red[1], red[5]), red[2], red[4]);
+    bad |= Ar::bad_pivot(det);
+    const T rdet = Ar::rcp(det);
+    const T f = Ar::mul(Ar::sub_mul(Ar::mul(red[3], red[5]), red[2], red[7]), rdet);
+    const T l = Ar::mul(Ar::sub_mul(Ar::mul(red[1], red[7]), red[4], red[3]), rdet);
+    oc_bwd<Ar>(A, lev.N, f, l);
+  }
+  __syncthreads();
+  oc_expand_levels<Ar>(lv, tid, lev);
+  if (tid < p) {
+    const T fl = lv[3][lvx(2 * tid)], ll = lv[3][lvx(2 * tid + 1)];
+    const AccL0<Ar, Tin> A{{s0[0], s0[1], s0[2], s0[3]}, tid * mt};
+    oc_bwd<Ar>(A, myL, fl, ll);
+  }
+  if (bad) atomicOr(status, ST_BAD_PIVOT);
+  __syncthreads();
+
+  // ---- the kept rows out (16-byte pieces where both the global row k0 and
+  // the shared-memory row o are whole pieces from aligned bases)
+  const int o = (int)(k0 - e0), K = (int)(k1 - k0);
+  const int kv = (vec16 && k0 % V == 0 && o % V == 0) ? K / V : 0;
+  for (int i = tid; i < kv; i += kWinThreads)
+    *reinterpret_cast<float4*>(x + k0 + i * V) =
+        *reinterpret_cast<const float4*>(s0[3] + o + i * V);
+  for (int i = kv * V + tid; i < K; i += kWinThreads) x[k0 + i] = s0[3][o + i];
+
+  // ---- the window's truncation bound
+  if (tid == 0) {
+    const float q = __uint_as_float(q_bits), bm = __uint_as_float(bmin_bits);
+    float eps;
+    if (cut_s[0] == 0.0f && cut_s[1] == 0.0f) {
+      eps = 0.0f;  // nothing cut
+    } else if (!(q < 1.0f) || !(bm > 0.0f)) {
+      eps = __int_as_float(0x7f800000);
+    } else {
+      const float num = cut_s[0] * powf(q, (float)o) + cut_s[1] * powf(q, (float)(e1 - k1));
+      eps = __fdiv_ru(num, __fmul_rd(1.0f - q, bm)) * (1.0f + 1e-5f);
+    }
+    atomicMax(bound_max, __float_as_uint(eps));
+    if (!(eps <= tol)) atomicOr(status, ST_NO_CONVERGENCE);
+  }
 }
 
 }  // namespace tps

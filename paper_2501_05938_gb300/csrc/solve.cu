@@ -14,6 +14,7 @@
 namespace tps {
 
 size_t onchip_exchange_bytes() { return (size_t)4 * 2 * kOcMaxCtas * 8; }
+int truncate_rows_max() { return kWinRowsMax; }
 
 // ------------------------------------------------------------------ on-chip solve
 struct OcGeom {
@@ -471,5 +472,45 @@ tps_status run_solve(tps_plan_s* P, int64_t n, const void* a, const void* b, con
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
   return e == cudaSuccess ? TPS_OK : TPS_ERR_CUDA;
 }
+
+// ------------------------------------------------------------------ windowed solve
+template <class Ar, class Tin>
+static cudaError_t launch_window(tps_plan_s* P, int64_t n, const Tin* a, const Tin* b,
+                                 const Tin* c, const Tin* d, Tin* x, cudaStream_t s) {
+  static bool done = false;  // the attribute allows the largest window
+  cudaError_t e = set_smem(k_window<Ar, Tin>, WinLayout<Ar, Tin>::bytes(kWinRowsMax), done);
+  if (e != cudaSuccess) return e;
+  const int R = P->m, h = P->m_reduced;
+  const size_t smem = WinLayout<Ar, Tin>::bytes(R + 2 * h);  // this window size
+  const int64_t windows = (n + R - 1) / R;
+  const uintptr_t al = (uintptr_t)a | (uintptr_t)b | (uintptr_t)c | (uintptr_t)d | (uintptr_t)x;
+  unsigned* bound = reinterpret_cast<unsigned*>(P->ws + 8);
+  e = cudaMemsetAsync(bound, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  const float tol = (float)(P->desc.tol > 0.0 ? P->desc.tol : 1e-12);
+  k_window<Ar, Tin><<<(unsigned)windows, kWinThreads, smem, s>>>(
+      n, R, h, a, b, c, d, x, tol, bound, P->d_status, (al % 16) == 0);
+  return cudaGetLastError();
+}
+
+tps_status run_truncated(tps_plan_s* P, int64_t n, const void* a, const void* b, const void* c,
+                         const void* d, void* x, cudaStream_t s) {
+  P->last_onchip = 0;
+  P->last_levels = 0;
+  cudaError_t e = cudaSuccess;
+  if (n <= kBaseMax) {
+    e = base_solve(P, n, a, b, c, d, x, s, nullptr, 0);
+  } else {
+    e = dispatch(P->desc.dtype, [&](auto ar, auto* tin, auto* tred) -> cudaError_t {
+      using Ar = decltype(ar);
+      using Tin = std::remove_pointer_t<decltype(tin)>;
+      (void)tred;
+      return launch_window<Ar, Tin>(P, n, (const Tin*)a, (const Tin*)b, (const Tin*)c,
+                                    (const Tin*)d, (Tin*)x, s);
+    });
+  }
+  return e == cudaSuccess ? TPS_OK : TPS_ERR_CUDA;
+}
+
 
 }  // namespace tps

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -59,6 +60,10 @@ static size_t workspace_for(tps_plan_s* P, size_t* off_levels_out, size_t* off_d
   P->off_xch = off;          // interface rows of the on-chip solve
   off = align_up(off + onchip_exchange_bytes());
   *off_levels_out = off;
+  if (P->desc.flags & TPS_TRUNCATE) {  // windows are solved on chip: no levels
+    *off_dev_out = off;
+    return off;
+  }
   std::vector<LevelPlan> lv;
   const size_t eio = elem_bytes_io(P->desc.dtype);
   const size_t ered = elem_bytes_red(P->desc.dtype);
@@ -109,12 +114,20 @@ tps_status tps_plan(const tps_plan_desc* desc, tps_plan_t* out) {
   if (d.dtype < TPS_F64 || d.dtype > TPS_F64_DF) return TPS_ERR_INVALID_ARG;
   if (d.residency != TPS_DEVICE && d.residency != TPS_HOST_PINNED) return TPS_ERR_INVALID_ARG;
   if (d.m != 0 && (d.m < 2 || d.m > (1 << 20))) return TPS_ERR_INVALID_ARG;
-  if (d.m_reduced != 0 && (d.m_reduced < 4 || d.m_reduced > (1 << 20))) return TPS_ERR_INVALID_ARG;
+  if (!(d.flags & TPS_TRUNCATE) && d.m_reduced != 0 && (d.m_reduced < 4 || d.m_reduced > (1 << 20)))
+    return TPS_ERR_INVALID_ARG;
   if (d.streams != 0 && (d.streams < 1 || d.streams > 32)) return TPS_ERR_INVALID_ARG;
   if (d.chunk < 0 || d.max_iters < 0 || d.tol < 0.0) return TPS_ERR_INVALID_ARG;
   if (d.flags & ~(TPS_TUNE_PREDICT | TPS_TUNE_EXHAUSTIVE | TPS_TRACE | TPS_EXTERNAL_WORKSPACE |
-                  TPS_GRAPH | TPS_ZERO_COPY | TPS_NO_ONCHIP))
+                  TPS_GRAPH | TPS_ZERO_COPY | TPS_NO_ONCHIP | TPS_TRUNCATE))
     return TPS_ERR_INVALID_ARG;
+  if (d.flags & TPS_TRUNCATE) {
+    // windows of m kept rows and m_reduced halo rows (both even, 0 = choose)
+    if (d.residency != TPS_DEVICE || d.dtype == TPS_MIXED_F32_F64) return TPS_ERR_UNSUPPORTED;
+    if ((d.m % 2) || (d.m_reduced % 2) || d.m_reduced < 0) return TPS_ERR_INVALID_ARG;
+    if ((int64_t)d.m + 2 * (int64_t)d.m_reduced > truncate_rows_max())
+      return TPS_ERR_INVALID_ARG;
+  }
   if ((d.flags & TPS_ZERO_COPY) && d.residency != TPS_HOST_PINNED) return TPS_ERR_INVALID_ARG;
 
   tps_plan_s* P = new (std::nothrow) tps_plan_s();
@@ -124,13 +137,27 @@ tps_status tps_plan(const tps_plan_desc* desc, tps_plan_t* out) {
   P->m_reduced = d.m_reduced;
   P->streams = d.streams;
   P->chunk = d.chunk;
-  if (d.flags & TPS_TUNE_PREDICT) {
+  if ((d.flags & TPS_TUNE_PREDICT) && !(d.flags & TPS_TRUNCATE)) {
     int32_t pm = 0, ps = 0;
     int64_t pc = 0;
     if (tps_predict_params(&d, &pm, &ps, &pc) == 0) {
       if (P->m == 0) P->m = pm;
       if (P->streams == 0) P->streams = ps;
       if (P->chunk == 0) P->chunk = pc;
+    }
+  }
+  if (d.flags & TPS_TRUNCATE) {
+    // halo for tol at a dominance factor of 3/4: q^h <= tol (1 - q) / 2
+    if (P->m_reduced == 0) {
+      const double tol = d.tol > 0.0 ? d.tol : 1e-12, q = 0.75;
+      int h = (int)std::ceil(std::log(tol * (1.0 - q) / 2.0) / std::log(q));
+      h += h & 1;
+      P->m_reduced = std::min(std::max(h, 2), truncate_rows_max() / 4);
+    }
+    if (P->m == 0) P->m = (truncate_rows_max() - 2 * P->m_reduced) & ~1;
+    if (P->m < 2) {
+      delete P;
+      return TPS_ERR_INVALID_ARG;
     }
   }
   default_params(d, P->m, P->m_reduced, P->streams);
@@ -328,6 +355,7 @@ tps_status tps_solve(tps_plan_t P, int64_t n, const void* a, const void* b, cons
   if (st != TPS_OK || n == 0) return st;
   cudaStream_t s = (cudaStream_t)stream;
   P->last_stream = s;
+  if (P->desc.flags & TPS_TRUNCATE) return run_truncated(P, n, a, b, c, d, x, s);
   std::vector<LevelPlan> lv;
   build_levels(n, P->m, P->m_reduced, elem_bytes_io(P->desc.dtype),
                elem_bytes_red(P->desc.dtype), P->off_levels, lv);
@@ -343,6 +371,7 @@ tps_status tps_solve_batched(tps_plan_t P, int64_t count, const int64_t* offsets
                              const void* c, const void* d, void* x, void* stream) {
   if (!P || count < 0 || (count > 0 && !offsets)) return TPS_ERR_INVALID_ARG;
   if (count > P->desc.batch_max) return TPS_ERR_INVALID_ARG;
+  if (P->desc.flags & TPS_TRUNCATE) return TPS_ERR_UNSUPPORTED;
   if (count == 0) return TPS_OK;
   if ((uintptr_t)offsets % 8) return TPS_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -479,6 +508,7 @@ tps_status tps_autotune(tps_plan_t P, int64_t n, int64_t count, const int64_t* o
                         const void* c, const void* d, void* x, void* stream, int32_t reps,
                         int32_t* best_m, float* best_ms) {
   if (!P || reps < 1 || count < 0) return TPS_ERR_INVALID_ARG;
+  if (P->desc.flags & TPS_TRUNCATE) return TPS_ERR_UNSUPPORTED;  // m is the window there
   cudaStream_t s = (cudaStream_t)stream;
   auto solve = [&]() -> tps_status {
     return count == 0 ? tps_solve(P, n, a, b, c, d, x, stream)
@@ -568,6 +598,14 @@ tps_status tps_plan_query(tps_plan_t P, tps_info* out) {
     status = TPS_ERR_NO_CONVERGENCE;
   P->host_status = TPS_OK;
   out->status = status;
+  if (P->desc.flags & TPS_TRUNCATE) {  // the largest window bound of the last solve
+    unsigned bits = 0;
+    if (cudaMemcpy(&bits, P->ws + 8, sizeof(bits), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return TPS_ERR_CUDA;
+    float bound;
+    std::memcpy(&bound, &bits, sizeof(bound));
+    out->last_correction = bound;
+  }
   return TPS_OK;
 }
 

@@ -120,6 +120,11 @@ cudaError_t stage3_range(tps_plan_s* P, const LevelPlan& L, int64_t kb, int64_t 
 cudaError_t reduced_solve(tps_plan_s* P, const std::vector<LevelPlan>& levels, cudaStream_t s);
 // Bytes of the on-chip solve's exchange rows (part of every plan workspace).
 size_t onchip_exchange_bytes();
+// TPS_TRUNCATE: the windowed solve of one device-resident system.
+tps_status run_truncated(tps_plan_s* P, int64_t n, const void* a, const void* b, const void* c,
+                         const void* d, void* x, cudaStream_t s);
+// Largest extended window (kept rows + both halos) of the windowed solve.
+int truncate_rows_max();
 // Copy `bytes` between host and device memory with a streaming kernel (SM
 // loads and stores, no copy engine); either side may be host memory the
 // device can address.  bytes and both pointers: multiples of 4.
