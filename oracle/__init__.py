@@ -13,6 +13,8 @@ Contents
     optimum-stream rule (Eq. 6), in plain Python.
   * ``mlp.py``: the launch-parameter MLP forward/backward in fp64 numpy.
   * ``refine.py``: mixed-precision iterative refinement, step by step.
+  * ``truncated.py``: truncated decoupling (windows with halos) and its
+    per-window error bound.
 
 Every function takes and returns numpy arrays; the C routines run on the
 host in plain fp64 (compiled with ``-ffp-contract=off``).
