@@ -221,10 +221,14 @@ tps_status tps_solve_host_async(tps_plan_t plan, int64_t n, const void* a, const
  *   n           0 .. TPS_NOALLOC_MAX_ROWS; larger n gives TPS_ERR_INVALID_ARG
  *   a, b, c, d  device inputs, x device output (n elements of the I/O type;
  *               x must not overlap an input), owned by the caller
- *   status_out  optional device int32 that receives TPS_OK or
- *               TPS_ERR_ZERO_PIVOT when the solve has run (NULL: not reported)
+ *   status_out  optional device int32 that receives TPS_OK,
+ *               TPS_ERR_ZERO_PIVOT or TPS_ERR_TIMEOUT when the solve has run
+ *               (NULL: not reported)
  *   stream      cudaStream_t as void*
- * Fixed parameters: m = 64 at the top level, 32 below.  The first call on a
+ * A system that fits in shared memory (every accepted size on a 152-SM
+ * GB300) is solved by the single-launch on-chip solve (see tps_solve);
+ * otherwise fixed parameters m = 64 at the top level, 32 below.  The first
+ * call on a
  * device looks up the scratch array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream
  * capture.  Every call overwrites the shared scratch, so calls whose work

@@ -5,8 +5,9 @@
 // where a cudaMalloc (which may synchronise the device) is not acceptable.
 // Instead of a plan and its workspace, this entry point keeps
 // its scratch (the reduced systems, the Stage-1 checkpoints and a status
-// word) in one fixed-size array in device global memory, declared at file
-// scope below.  Every GPU that loads the library holds that array
+// word; or, when the system fits on chip and is solved by one cooperative
+// launch, that launch's barrier counter and exchange rows) in one
+// fixed-size array in device global memory, declared at file scope below.  Every GPU that loads the library holds that array
 // (kScratchBytes) until the process exits.  All calls share it, and it keeps
 // whatever the last call left there; so two calls whose work overlaps on
 // the GPU (different streams, or different host threads) race on it and
@@ -170,7 +171,13 @@ extern "C" tps_status tps_solve_noalloc(int32_t dtype, int64_t n, const void* a,
   // the status word is the only scratch that must start from zero; the
   // reduced systems and checkpoints are fully rewritten by every call
   cudaError_t e = cudaMemsetAsync(st, 0, sizeof(int), s);
-  if (e == cudaSuccess) {
+  // the whole system in one on-chip launch where it fits (its barrier
+  // counter and exchange rows sit where the levels would go)
+  bool onchip = false;
+  if (e == cudaSuccess)
+    e = onchip_solve(dtype, n, a, b, c, d, x, ws + align_up(64), reinterpret_cast<unsigned*>(ws + 32),
+                     st, s, onchip);
+  if (e == cudaSuccess && !onchip) {
     switch (dtype) {
       case TPS_F64:
         e = run<ArF64, double, double>(ws, L, 0, n, (const double*)a, (const double*)b,

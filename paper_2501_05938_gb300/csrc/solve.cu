@@ -68,18 +68,18 @@ static int oc_ctas_max() {
   return cache[dev];
 }
 
-// Solve the system on chip if it fits (used = true), else leave it.
+// Solve the system on chip if it fits (used = true), else leave it.  xch:
+// onchip_exchange_bytes() of device memory; bar: a counter (zeroed here).
 template <class Ar, class Tin>
-static cudaError_t launch_onchip(tps_plan_s* P, int64_t n, const Tin* a, const Tin* b,
-                                 const Tin* c, const Tin* d, Tin* x, cudaStream_t s,
-                                 bool& used) {
+static cudaError_t launch_onchip_raw(int64_t n, const Tin* a, const Tin* b, const Tin* c,
+                                     const Tin* d, Tin* x, void* xch_bytes, unsigned* bar,
+                                     int* status, bool extra_arrival, cudaStream_t s,
+                                     bool& used) {
   used = false;
-  if (P->desc.flags & TPS_NO_ONCHIP) return cudaSuccess;
   OcGeom g;
   if (!oc_geometry<Tin>(n, oc_ctas_max<Ar, Tin>(), g)) return cudaSuccess;
-  unsigned* bar = reinterpret_cast<unsigned*>(P->ws + 32);
   using T = typename Ar::T;
-  T* xch = reinterpret_cast<T*>(P->ws + P->off_xch);
+  T* xch = reinterpret_cast<T*>(xch_bytes);
   const uintptr_t al = (uintptr_t)a | (uintptr_t)b | (uintptr_t)c | (uintptr_t)d | (uintptr_t)x;
   const int vec16 = (al % 16) == 0;
   cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), s);
@@ -94,11 +94,22 @@ static cudaError_t launch_onchip(tps_plan_s* P, int64_t n, const Tin* a, const T
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const unsigned arrivals = (unsigned)g.G + (P->test_barrier_extra ? 1u : 0u);
+  const unsigned arrivals = (unsigned)g.G + (extra_arrival ? 1u : 0u);
   e = cudaLaunchKernelEx(&cfg, k_onchip<Ar, Tin>, n, g.mt, g.p, a, b, c, d, x, xch, bar,
-                         arrivals, P->d_status, vec16);
+                         arrivals, status, vec16);
   if (e == cudaSuccess) used = true;
   return e;
+}
+
+template <class Ar, class Tin>
+static cudaError_t launch_onchip(tps_plan_s* P, int64_t n, const Tin* a, const Tin* b,
+                                 const Tin* c, const Tin* d, Tin* x, cudaStream_t s,
+                                 bool& used) {
+  used = false;
+  if (P->desc.flags & TPS_NO_ONCHIP) return cudaSuccess;
+  return launch_onchip_raw<Ar, Tin>(n, a, b, c, d, x, P->ws + P->off_xch,
+                                    reinterpret_cast<unsigned*>(P->ws + 32), P->d_status,
+                                    P->test_barrier_extra, s, used);
 }
 
 Level make_level(int64_t n, int m, int R) {
@@ -512,5 +523,17 @@ tps_status run_truncated(tps_plan_s* P, int64_t n, const void* a, const void* b,
   return e == cudaSuccess ? TPS_OK : TPS_ERR_CUDA;
 }
 
+
+cudaError_t onchip_solve(int dtype, int64_t n, const void* a, const void* b, const void* c,
+                         const void* d, void* x, void* xch, unsigned* bar, int* status,
+                         cudaStream_t s, bool& used) {
+  return dispatch(dtype, [&](auto ar, auto* tin, auto* tred) -> cudaError_t {
+    using Ar = decltype(ar);
+    using Tin = std::remove_pointer_t<decltype(tin)>;
+    (void)tred;
+    return launch_onchip_raw<Ar, Tin>(n, (const Tin*)a, (const Tin*)b, (const Tin*)c,
+                                      (const Tin*)d, (Tin*)x, xch, bar, status, false, s, used);
+  });
+}
 
 }  // namespace tps

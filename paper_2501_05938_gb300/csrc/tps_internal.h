@@ -120,6 +120,13 @@ cudaError_t stage3_range(tps_plan_s* P, const LevelPlan& L, int64_t kb, int64_t 
 cudaError_t reduced_solve(tps_plan_s* P, const std::vector<LevelPlan>& levels, cudaStream_t s);
 // Bytes of the on-chip solve's exchange rows (part of every plan workspace).
 size_t onchip_exchange_bytes();
+// The single-launch on-chip solve of one system if it fits on this device
+// (used = true), else nothing.  xch: onchip_exchange_bytes() of device
+// memory; bar: a device counter (zeroed by the call); status: the device
+// status word.
+cudaError_t onchip_solve(int dtype, int64_t n, const void* a, const void* b, const void* c,
+                         const void* d, void* x, void* xch, unsigned* bar, int* status,
+                         cudaStream_t s, bool& used);
 // TPS_TRUNCATE: the windowed solve of one device-resident system.
 tps_status run_truncated(tps_plan_s* P, int64_t n, const void* a, const void* b, const void* c,
                          const void* d, void* x, cudaStream_t s);
