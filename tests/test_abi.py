@@ -57,6 +57,33 @@ def test_plan_rejects_bad_descriptors_on_the_host(lib, field, value):
     assert not h.value
 
 
+@pytest.mark.parametrize("fields,status", [
+    ({"flags": 128, "m": 101}, 1),                     # odd window
+    ({"flags": 128, "m_reduced": 3}, 1),               # odd halo
+    ({"flags": 128, "m": 1500, "m_reduced": 200}, 1),  # window + halos above 1792 rows
+    ({"flags": 128, "m_reduced": -2}, 1),
+    ({"flags": 128, "residency": 1}, 2),               # truncation is device-resident only
+    ({"flags": 128, "dtype": 2}, 2),                   # and not for the refinement dtype
+    ({"flags": 32 | 128, "residency": 1}, 2),
+])
+def test_truncate_descriptor_checks_on_the_host(lib, fields, status):
+    d = binding.PlanDesc(n_max=1000, dtype=0)
+    for k, v in fields.items():
+        setattr(d, k, v)
+    h = ctypes.c_void_p()
+    assert lib.tps_plan(ctypes.byref(d), ctypes.byref(h)) == status
+    assert not h.value
+
+
+def test_flag_constants_match_the_header():
+    hdr = open(os.path.join(ROOT, "include", "tps.h")).read()
+    for name, val in (("TPS_GRAPH", binding.GRAPH), ("TPS_ZERO_COPY", binding.ZERO_COPY),
+                      ("TPS_NO_ONCHIP", binding.NO_ONCHIP), ("TPS_TRUNCATE", binding.TRUNCATE),
+                      ("TPS_TRACE", binding.TRACE), ("TPS_TUNE_PREDICT", binding.TUNE_PREDICT)):
+        m = re.search(r"#define\s+" + name + r"\s+(\d+)u", hdr)
+        assert m and int(m.group(1)) == val, name
+
+
 def test_null_arguments(lib):
     h = ctypes.c_void_p()
     assert lib.tps_plan(None, ctypes.byref(h)) == 1
