@@ -16,8 +16,8 @@ Stage 2, Stage 3).
            D2H) in the same run, the bound no pipeline can beat
            (e2e.zero_copy: the same through TPS_ZERO_COPY, kernels reading
            and writing pinned, and pageable, host memory directly)
-  batched  4096 packed systems, n_i log-uniform in [2^8, 2^20] (--no-extra
-           skips this and the next)
+  batched  4096 packed systems, n_i log-uniform in [2^8, 2^20], each solve
+           one graph launch (--no-extra skips this and the next)
   mixed    the refinement workload (b = 1.01 (|a| + |c|)) in every arithmetic
   midsize_f64_df  n = 65536 and 800000: the single-launch on-chip solve
            against the level-by-level route (L2-warm)
@@ -367,7 +367,8 @@ def extra_workloads(binding, synth, world, rank, stream, a):
         tdt = torch.float32 if dt == "f32" else torch.float64
         arrs = [gb[k].to(tdt) for k in "abcd"]
         x = torch.empty(nb, dtype=tdt, device="cuda")
-        plan = binding.Plan(nb, dtype=dt, batch_max=4096, flags=binding.TUNE_PREDICT)
+        plan = binding.Plan(nb, dtype=dt, batch_max=4096,
+                            flags=binding.TUNE_PREDICT | binding.GRAPH)
         steps = max(3, a.steps // 10)
         for _ in range(2):
             plan.solve_batched(offs, *arrs, x, host_offsets=off, stream=stream)

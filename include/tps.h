@@ -71,7 +71,7 @@ typedef enum {
 #define TPS_TUNE_EXHAUSTIVE 2u    /* time the candidate grid on the device        */
 #define TPS_TRACE 4u              /* record per-stage event times (tps_plan_query) */
 #define TPS_EXTERNAL_WORKSPACE 8u /* caller supplies the workspace                */
-#define TPS_GRAPH 16u             /* replay Stage 2 as one CUDA graph launch      */
+#define TPS_GRAPH 16u             /* replay the solve as one CUDA graph launch    */
 #define TPS_ZERO_COPY 32u         /* host residency: kernels, not copy engines,   */
                                   /* move host data (see tps_solve_host_async)    */
 #define TPS_NO_ONCHIP 64u         /* never use the single-launch on-chip solve    */
@@ -140,11 +140,14 @@ tps_status tps_set_workspace(tps_plan_t plan, void* dev_ptr, size_t bytes);
  * the kernels on `stream` and returns; no host synchronisation, so it may
  * be captured into a CUDA graph (except TPS_MIXED_F32_F64, which reads its
  * convergence test back to the host after every correction).  With
- * TPS_GRAPH the plan captures Stage 2 -- the recursive solve of the reduced
- * system, a chain of small launches that touches only the workspace -- into
- * a CUDA graph on a private stream at the first solve with a given level
- * geometry, and replays it as one graph launch afterwards (also from
- * tps_solve_batched and the host pipeline).
+ * TPS_GRAPH the plan captures the whole solve (every launch of Stages 1-3)
+ * into a CUDA graph on a private stream at the first call with a given size,
+ * geometry and set of pointers, and replays it as one graph launch while
+ * they stay the same (also tps_solve_batched, whose offsets pointer is part
+ * of the key); new pointers or sizes recapture.  With TPS_TRACE as well, or
+ * in the host pipeline, only Stage 2 -- the recursive solve of the reduced
+ * system, a chain of small launches that touches only the workspace -- is
+ * captured, keyed by its level geometry, so the stage events stay apart.
  *
  * A system that fits in the GPU's shared memory (up to ~0.89 M rows in
  * fp64 and double-float, ~1.8 M in fp32 on 152 SMs; not for packed batches)

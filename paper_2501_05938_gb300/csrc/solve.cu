@@ -446,9 +446,69 @@ cudaError_t reduced_solve_graph(tps_plan_s* P, const std::vector<LevelPlan>& lev
   return cudaGraphLaunch(P->graph, s);
 }
 
+static tps_status run_solve_direct(tps_plan_s* P, int64_t n, const void* a, const void* b,
+                                   const void* c, const void* d, void* x, cudaStream_t s,
+                                   const std::vector<LevelPlan>& lv, cudaEvent_t* ev,
+                                   const int64_t* bnd, int64_t nbnd);
+
+// TPS_GRAPH without stage events: capture the whole solve on the plan's
+// private stream the first time a geometry and set of pointers is seen,
+// then replay it as one graph launch.  Everything the captured launches
+// read from the host (sizes, pointers, the level plan) is in the key.
+static tps_status run_solve_graph(tps_plan_s* P, int64_t n, const void* a, const void* b,
+                                  const void* c, const void* d, void* x, cudaStream_t s,
+                                  const std::vector<LevelPlan>& lv, const int64_t* bnd,
+                                  int64_t nbnd) {
+  const int64_t key[16] = {n, (int64_t)a, (int64_t)b, (int64_t)c, (int64_t)d, (int64_t)x,
+                           (int64_t)bnd, nbnd, P->m, P->m_reduced, (int64_t)lv.size(),
+                           (int64_t)P->ws, P->desc.dtype, (int64_t)P->desc.flags, 0, 0};
+  bool same = P->solve_graph != nullptr;
+  for (int i = 0; i < 16 && same; ++i) same = P->sgkey[i] == key[i];
+  if (!same) {
+    if (P->solve_graph) {
+      cudaGraphExecDestroy(P->solve_graph);
+      P->solve_graph = nullptr;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!P->cap_stream) e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return TPS_ERR_CUDA;
+    const tps_status st = run_solve_direct(P, n, a, b, c, d, x, P->cap_stream, lv, nullptr, bnd,
+                                           nbnd);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(P->cap_stream, &g);
+    if (st != TPS_OK || e != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return st != TPS_OK ? st : TPS_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&P->solve_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      P->solve_graph = nullptr;
+      return TPS_ERR_CUDA;
+    }
+    for (int i = 0; i < 16; ++i) P->sgkey[i] = key[i];
+    P->sg_onchip = P->last_onchip;
+    P->sg_levels = P->last_levels;
+  }
+  P->last_onchip = P->sg_onchip;
+  P->last_levels = P->sg_levels;
+  return cudaGraphLaunch(P->solve_graph, s) == cudaSuccess ? TPS_OK : TPS_ERR_CUDA;
+}
+
 tps_status run_solve(tps_plan_s* P, int64_t n, const void* a, const void* b, const void* c,
                      const void* d, void* x, cudaStream_t s, const std::vector<LevelPlan>& lv,
                      cudaEvent_t* ev, const int64_t* bnd, int64_t nbnd) {
+  if ((P->desc.flags & TPS_GRAPH) && !ev && P->desc.dtype != TPS_MIXED_F32_F64)
+    return run_solve_graph(P, n, a, b, c, d, x, s, lv, bnd, nbnd);
+  return run_solve_direct(P, n, a, b, c, d, x, s, lv, ev, bnd, nbnd);
+}
+
+static tps_status run_solve_direct(tps_plan_s* P, int64_t n, const void* a, const void* b,
+                                   const void* c, const void* d, void* x, cudaStream_t s,
+                                   const std::vector<LevelPlan>& lv, cudaEvent_t* ev,
+                                   const int64_t* bnd, int64_t nbnd) {
   cudaError_t e = cudaSuccess;
   P->last_onchip = 0;
   if (ev) e = cudaEventRecord(ev[0], s);
@@ -475,8 +535,11 @@ tps_status run_solve(tps_plan_s* P, int64_t n, const void* a, const void* b, con
   } else {
     if (e == cudaSuccess) e = stage1_range(P, lv[0], 0, lv[0].lv.p, a, b, c, d, s);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
+    // with stage events (TPS_TRACE) TPS_GRAPH captures Stage 2 alone; without
+    // them the whole solve is one graph already (run_solve_graph)
     if (e == cudaSuccess)
-      e = (P->desc.flags & TPS_GRAPH) ? reduced_solve_graph(P, lv, s) : reduced_solve(P, lv, s);
+      e = ((P->desc.flags & TPS_GRAPH) && ev) ? reduced_solve_graph(P, lv, s)
+                                              : reduced_solve(P, lv, s);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
     if (e == cudaSuccess) e = stage3_range(P, lv[0], 0, lv[0].lv.p, a, b, c, d, x, s);
   }

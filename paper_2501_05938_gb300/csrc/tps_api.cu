@@ -265,6 +265,7 @@ tps_status tps_plan_destroy(tps_plan_t P) {
     delete[] P->trace_ev;
   }
   if (P->graph) cudaGraphExecDestroy(P->graph);
+  if (P->solve_graph) cudaGraphExecDestroy(P->solve_graph);
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   if (P->ws_owned && P->ws) cudaFree(P->ws);
   if (P->d_work) cudaFree(P->d_work);

@@ -79,6 +79,11 @@ struct tps_plan_s {
   cudaGraphExec_t graph = nullptr;
   cudaStream_t cap_stream = nullptr;
   int64_t gkey[12] = {};
+  // TPS_GRAPH without TPS_TRACE: the whole solve, captured once per
+  // geometry and set of pointers, replayed as one graph launch
+  cudaGraphExec_t solve_graph = nullptr;
+  int64_t sgkey[16] = {};
+  int32_t sg_onchip = 0, sg_levels = 0;
   // TPS_ZERO_COPY: the device can read and write pageable host memory
   bool pageable_ok = false;
   // on-chip solve: exchange rows for the CTAs' interface equations, and

@@ -322,6 +322,32 @@ def test_graph_mode_replays_and_recaptures():
     assert oracle.rel_forward_error(x.cpu().numpy(), ref) <= F64_FWD
 
 
+@pytest.mark.parametrize("n", [300001, (1 << 21) + 3])
+def test_whole_solve_graph_replays_and_recaptures(n):
+    """TPS_GRAPH without TRACE: the whole solve (on chip, or level by level
+    with an on-chip Stage 2) is one graph; new data in the same buffers is
+    solved by the replay, new pointers recapture."""
+    plan = binding.Plan(n, dtype="f64_df", flags=binding.GRAPH)
+    bufs = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(5)]
+    for seed in (1, 2):
+        s = synth.system(seed, n)
+        for t, k in zip(bufs, "abcd"):
+            t.copy_(torch.as_tensor(s[k]))
+        bufs[4].fill_(float("nan"))
+        plan.solve(*bufs)
+        torch.cuda.synchronize()
+        ref = oracle.thomas(s["a"], s["b"], s["c"], s["d"])
+        assert oracle.rel_forward_error(bufs[4].cpu().numpy(), ref) <= F64_FWD
+        assert plan.query()["status"] == 0
+    s = synth.system(3, n - 4)
+    a, b, c, d = (torch.as_tensor(s[k]).cuda() for k in "abcd")
+    x = torch.empty_like(b)
+    plan.solve(a, b, c, d, x)
+    torch.cuda.synchronize()
+    ref = oracle.thomas(s["a"], s["b"], s["c"], s["d"])
+    assert oracle.rel_forward_error(x.cpu().numpy(), ref) <= F64_FWD
+
+
 def test_graph_mode_batched():
     sizes = [1000, 1, 0, 4097, 300]
     off = synth.offsets_from_sizes(sizes)
