@@ -84,11 +84,14 @@ typedef struct {
   int32_t dtype;     /* tps_dtype                                              */
   int32_t residency; /* tps_residency (informs the predictor)                  */
   int32_t m;         /* rows per block at the top level; 0 = choose            */
-  int32_t m_reduced; /* rows per block at the recursive levels; 0 = choose     */
+                     /* (TPS_TRUNCATE: kept rows per window, even)             */
+  int32_t m_reduced; /* rows per block at the recursive levels (>= 4); 0 =     */
+                     /* choose (TPS_TRUNCATE: halo rows per side, even)        */
   int32_t streams;   /* S for tps_solve_host_async (1..32); 0 = choose         */
   int32_t max_iters; /* refinement iteration cap; 0 = 10                       */
   int64_t chunk;     /* rows per host-pipeline chunk; 0 = choose               */
   double tol;        /* refinement stop: ||delta||/||x|| <= tol; 0 = 1e-12     */
+                     /* (TPS_TRUNCATE: the largest accepted error bound)       */
   uint32_t flags;    /* TPS_TUNE_* | TPS_TRACE | TPS_EXTERNAL_WORKSPACE |      */
                      /* TPS_GRAPH | TPS_ZERO_COPY | TPS_NO_ONCHIP |            */
                      /* TPS_TRUNCATE                                           */
@@ -116,10 +119,14 @@ typedef struct {
 } tps_info;
 
 /* Create a plan.  Validates `desc` (n_max >= 0, dtype, m 0 or >= 2, streams
- * 0 or 1..32, reserved == 0), resolves zero parameters (predictor when
- * TPS_TUNE_PREDICT is set, fixed defaults otherwise), creates the streams
- * and events of the host pipeline and, unless TPS_EXTERNAL_WORKSPACE is set,
- * allocates the device workspace.  On failure *out is NULL. */
+ * 0 or 1..32, known flags, reserved == 0; TPS_ZERO_COPY needs host
+ * residency, TPS_TRUNCATE device residency and a non-mixed dtype), resolves
+ * zero parameters (predictor when TPS_TUNE_PREDICT is set, fixed defaults
+ * otherwise), creates the streams and events of the host pipeline and,
+ * unless TPS_EXTERNAL_WORKSPACE is set, allocates the device workspace.
+ * Returns TPS_ERR_INVALID_ARG or TPS_ERR_UNSUPPORTED for a bad descriptor,
+ * TPS_ERR_OOM if the workspace cannot be allocated.  On failure *out is
+ * NULL. */
 tps_status tps_plan(const tps_plan_desc* desc, tps_plan_t* out);
 
 /* Release everything the plan owns (not a caller-supplied workspace).  The
