@@ -292,8 +292,6 @@ def verify(g, x):
 def cpu_oracle_leg(g, x_gpu, budget_s=12.0):
     """The serial Thomas oracle on the full system; returns the throughput
     and the GPU result's relative forward error against it."""
-    import numpy as np
-
     import oracle
 
     a, b, c, d = (g[k].cpu().numpy() for k in "abcd")

@@ -1,7 +1,6 @@
 """Mixed-precision refinement (fp32 partition elimination, fp64 residual and
 update) against the fp64 Thomas oracle, on the dominance ratios of the
 refinement workload (b = r (|a| + |c|), r in {1.01, 1.1, 2.0})."""
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")

@@ -3,8 +3,6 @@ eliminates its rows in shared memory, one grid barrier, the CTA interface
 system by parallel cyclic reduction, recovery on chip) against the CPU
 oracle, at its capacity edges, as the Stage 2 of larger solves, inside a
 captured CUDA graph, and with its barrier wait made to run out."""
-import os
-
 import numpy as np
 import pytest
 

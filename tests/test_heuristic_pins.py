@@ -3,7 +3,6 @@ the paper prints in Tables 1, 2, 4 and 5."""
 import math
 
 import numpy as np
-import pytest
 
 from oracle import heuristic as H
 

@@ -1,5 +1,4 @@
 """Pins for the step-by-step mixed-precision refinement oracle."""
-import numpy as np
 import pytest
 
 import oracle

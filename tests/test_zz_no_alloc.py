@@ -6,7 +6,6 @@ even though they share the library's fixed scratch array.  This file is
 named so that pytest collects it last."""
 import ctypes
 
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
