@@ -426,7 +426,10 @@ __global__ void __launch_bounds__(W * 32)
   static_assert(sizeof(Tred) == 4 || sizeof(Tred) == 8, "checkpoint element size");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t k0 = lv.k_begin + ((int64_t)blockIdx.x * W + warp) * 32;
+  // CTAs run in the reverse of Stage 1's order: the rows Stage 1 read last
+  // are the ones still in L2 (and the next solve's Stage 1 starts on the
+  // rows this one read last)
+  const int64_t k0 = lv.k_begin + ((int64_t)(gridDim.x - 1 - blockIdx.x) * W + warp) * 32;
   if (k0 >= lv.k_end) return;
   const int nb = (int)(lv.k_end - k0 < 32 ? lv.k_end - k0 : 32);
   const int64_t k = k0 + lane;
