@@ -309,9 +309,20 @@ def cpu_oracle_leg(g, x_gpu, budget_s=12.0):
     err = oracle.rel_forward_error(xg, ref)
     res = oracle.rel_residual(a, b, c, d, xg)
     best = min(times)
+    # the serial partition oracle (the method's three stages on one core),
+    # best of 3 on a 2^23-row prefix of the same system, for context
+    k = min(n, 1 << 23)
+    tp = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        oracle.partition(a[:k], b[:k], c[:k], d[:k], 128)
+        tp.append(time.perf_counter() - t0)
     return {"value": n / best, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"serial fp64 Thomas oracle on the full n={n} system, best of "
-                      f"{len(times)} solves ({sum(times):.1f} s of CPU work)"}, err, res, ref
+                      f"{len(times)} solves ({sum(times):.1f} s of CPU work)",
+            "partition_value": k / min(tp),
+            "partition_sample": f"serial fp64 partition oracle (m = 128), best of 3 solves "
+                                f"of the first {k} rows"}, err, res, ref
 
 
 def workload_name(n):
