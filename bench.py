@@ -528,6 +528,10 @@ def main():
         hx = torch.empty(n, dtype=torch.float64).pin_memory()
         plan_h = binding.Plan(n, dtype="f64_df", residency="host", m=a.m, m_reduced=a.m_reduced,
                               streams=a.streams, chunk=a.chunk, flags=binding.TUNE_PREDICT)
+        pred_h = plan_h.query()
+        if not a.streams and not a.chunk:
+            # the predicted (S, chunk) refined on this machine's link by the exhaustive search
+            plan_h.autotune(hk["a"], hk["b"], hk["c"], hk["d"], hx, reps=1, stream=stream)
         esteps = a.e2e_steps or max(3, min(a.steps, 20))
         for _ in range(min(a.warmup, 3)):
             plan_h.solve_host_async(hk["a"], hk["b"], hk["c"], hk["d"], hx, stream=stream)
@@ -602,6 +606,7 @@ def main():
         "e2e": {"value": world * n / (ems * 1e-3), "unit": UNIT, "ms_per_step": ems,
                 "steps": esteps, "h2d_bytes_per_step": 4 * 8 * n, "d2h_bytes_per_step": 8 * n,
                 "streams": infoh["streams"], "chunk": infoh["chunk"],
+                "predicted": {"streams": pred_h["streams"], "chunk": pred_h["chunk"]},
                 "link_floor_ms": floor_ms, "frac_of_link_floor": floor_ms / ems,
                 "rel_fwd_vs_x_true": eh_err, "zero_copy": zc},
         "clocks": clocks,

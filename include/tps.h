@@ -310,7 +310,13 @@ int tps_predict_load(const char* path);
  * `reps` timed solves each after one warm-up, and keep the fastest m in the
  * plan.  A plan created with TPS_TUNE_EXHAUSTIVE sizes its workspace for the
  * whole grid.  Synchronises `stream`; x is overwritten.  *best_m and
- * *best_ms (may be NULL) receive the choice and its mean time. */
+ * *best_ms (may be NULL) receive the choice and its mean time.
+ * For a host-residency plan (count must be 0, a..x pinned or, with
+ * TPS_ZERO_COPY, host memory as tps_solve_host_async accepts) the search is
+ * over the stream count S in {1, 2, 4, 8, 16, 32} and the chunk in
+ * {n/S, 2^22, 2^24 rows} through tps_solve_host_async instead, and the
+ * fastest (S, chunk) is kept (tps_plan_query reports them); the plan's
+ * stream set grows to 32 streams. */
 tps_status tps_autotune(tps_plan_t plan, int64_t n, int64_t count, const int64_t* offsets,
                         const int64_t* host_offsets, const void* a, const void* b,
                         const void* c, const void* d, void* x, void* stream, int32_t reps,

@@ -31,6 +31,25 @@ static tps_status cuda_status(cudaError_t e) {
 }
 
 constexpr int kTraceSlots = 256;
+
+// Streams and events of the host pipeline, grown to at least S.
+static cudaError_t ensure_streams(HostPipe* H, int S) {
+  cudaError_t e = cudaSuccess;
+  while ((int)H->streams.size() < S && e == cudaSuccess) {
+    cudaStream_t s;
+    cudaEvent_t e1, e3;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) break;
+    H->streams.push_back(s);
+    e = cudaEventCreateWithFlags(&e1, cudaEventDisableTiming);
+    if (e != cudaSuccess) break;
+    H->ev_done1.push_back(e1);
+    e = cudaEventCreateWithFlags(&e3, cudaEventDisableTiming);
+    if (e != cudaSuccess) break;
+    H->ev_done3.push_back(e3);
+  }
+  return e;
+}
 constexpr int32_t kTuneMin = 16, kTuneMax = 1024;  // autotuner block-size grid
 
 static cudaEvent_t* next_trace(tps_plan_s* P) {
@@ -196,19 +215,7 @@ tps_status tps_plan(const tps_plan_desc* desc, tps_plan_t* out) {
     H->off_dev = off_dev;
     cudaError_t e = cudaEventCreateWithFlags(&H->ev_start, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&H->ev_red, cudaEventDisableTiming);
-    for (int i = 0; i < P->streams && e == cudaSuccess; ++i) {
-      cudaStream_t s;
-      cudaEvent_t e1, e3;
-      e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-      if (e != cudaSuccess) break;
-      H->streams.push_back(s);
-      e = cudaEventCreateWithFlags(&e1, cudaEventDisableTiming);
-      if (e != cudaSuccess) break;
-      H->ev_done1.push_back(e1);
-      e = cudaEventCreateWithFlags(&e3, cudaEventDisableTiming);
-      if (e != cudaSuccess) break;
-      H->ev_done3.push_back(e3);
-    }
+    if (e == cudaSuccess) e = ensure_streams(H, P->streams);
     if (e != cudaSuccess) {
       tps_plan_destroy(P);
       return cuda_status(e);
@@ -436,7 +443,7 @@ tps_status tps_solve_host_async(tps_plan_t P, int64_t n, const void* a, const vo
   std::vector<LevelPlan> lv;
   build_levels(n, P->m, P->m_reduced, es, elem_bytes_red(P->desc.dtype), P->off_levels, lv);
   P->last_levels = (int32_t)lv.size();
-  const int S = (int)H->streams.size();
+  const int S = P->streams;  // the plan's S (the pipe may hold more streams)
   cudaError_t e = cudaEventRecord(H->ev_start, us);
   for (int i = 0; i < S && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(H->streams[i], H->ev_start, 0);
   if (e != cudaSuccess) return TPS_ERR_CUDA;
@@ -504,12 +511,79 @@ tps_status tps_solve_host_async(tps_plan_t P, int64_t n, const void* a, const vo
   return e == cudaSuccess ? TPS_OK : TPS_ERR_CUDA;
 }
 
+}  // extern "C"
+
+namespace tps {
+
+// Exhaustive search of a host-residency plan: the stream count S over
+// {1, 2, 4, 8, 16, 32} and the chunk over {n/S, 2^22, 2^24 rows} on the
+// caller's pinned arrays; keeps the fastest (S, chunk) in the plan.
+static tps_status autotune_host(tps_plan_s* P, int64_t n, const void* a, const void* b,
+                                const void* c, const void* d, void* x, void* stream,
+                                int32_t reps, int32_t* best_m, float* best_ms) {
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return TPS_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return TPS_ERR_CUDA;
+  }
+  const int32_t keep_S = P->streams;
+  const int64_t keep_chunk = P->chunk;
+  int32_t bS = keep_S;
+  int64_t bc = keep_chunk;
+  float best_t = -1.0f;
+  tps_status st = TPS_OK;
+  if (ensure_streams(P->pipe, 32) != cudaSuccess) st = TPS_ERR_CUDA;
+  const int64_t chunks[3] = {0, (int64_t)1 << 22, (int64_t)1 << 24};
+  for (int32_t S = 1; S <= 32 && st == TPS_OK; S *= 2) {
+    for (int ci = 0; ci < 3 && st == TPS_OK; ++ci) {
+      if (chunks[ci] && chunks[ci] * 2 > n) continue;  // fewer than two chunks: same as n/S
+      P->streams = S;
+      P->chunk = chunks[ci];
+      st = tps_solve_host_async(P, n, a, b, c, d, x, stream);  // warm-up
+      if (st != TPS_OK) break;
+      if (cudaEventRecord(e0, s) != cudaSuccess) { st = TPS_ERR_CUDA; break; }
+      for (int r = 0; r < reps && st == TPS_OK; ++r)
+        st = tps_solve_host_async(P, n, a, b, c, d, x, stream);
+      if (st != TPS_OK) break;
+      float ms = 0.0f;
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        st = TPS_ERR_CUDA;
+        break;
+      }
+      ms /= reps;
+      if (best_t < 0.0f || ms < best_t) {
+        best_t = ms;
+        bS = S;
+        bc = chunks[ci];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const bool ok = st == TPS_OK && best_t >= 0.0f;
+  P->streams = ok ? bS : keep_S;
+  P->chunk = ok ? bc : keep_chunk;
+  if (best_m) *best_m = P->m;
+  if (best_ms) *best_ms = best_t;
+  return st;
+}
+
+}  // namespace tps
+
+extern "C" {
+
 tps_status tps_autotune(tps_plan_t P, int64_t n, int64_t count, const int64_t* offsets,
                         const int64_t* host_offsets, const void* a, const void* b,
                         const void* c, const void* d, void* x, void* stream, int32_t reps,
                         int32_t* best_m, float* best_ms) {
   if (!P || reps < 1 || count < 0) return TPS_ERR_INVALID_ARG;
   if (P->desc.flags & TPS_TRUNCATE) return TPS_ERR_UNSUPPORTED;  // m is the window there
+  if (P->pipe)  // host residency: S and chunk instead of m
+    return count ? TPS_ERR_INVALID_ARG
+                 : autotune_host(P, n, a, b, c, d, x, stream, reps, best_m, best_ms);
   cudaStream_t s = (cudaStream_t)stream;
   auto solve = [&]() -> tps_status {
     return count == 0 ? tps_solve(P, n, a, b, c, d, x, stream)

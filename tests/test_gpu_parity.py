@@ -206,6 +206,26 @@ def test_host_pipeline_matches_oracle(dtype, n, m, S, chunk):
     assert oracle.rel_residual(s["a"], s["b"], s["c"], s["d"], xs) <= F64_RES
 
 
+@pytest.mark.parametrize("flags", [0, binding.ZERO_COPY])
+def test_host_autotune_keeps_a_working_stream_and_chunk_choice(flags):
+    n = 2_000_003
+    s = synth.system(77, n)
+    plan = binding.Plan(n, dtype="f64_df", residency="host", streams=2, flags=flags)
+    a, b, c, d = (pinned(s[k]) for k in "abcd")
+    x = torch.empty(n, dtype=torch.float64).pin_memory()
+    stream = torch.cuda.Stream()
+    _, ms = plan.autotune(a, b, c, d, x, reps=1, stream=stream)
+    info = plan.query()
+    assert ms > 0 and info["streams"] in (1, 2, 4, 8, 16, 32)
+    assert info["chunk"] in (0, 1 << 22, 1 << 24)
+    x.fill_(float("nan"))
+    plan.solve_host_async(a, b, c, d, x, stream=stream)
+    stream.synchronize()
+    assert plan.query()["status"] == 0
+    ref = oracle.thomas(s["a"], s["b"], s["c"], s["d"])
+    assert oracle.rel_forward_error(x.numpy(), ref) <= F64_FWD
+
+
 def test_host_pipeline_rejects_pageable_and_device_memory():
     n = 1000
     plan = binding.Plan(n, dtype="f64", residency="host", streams=2)
