@@ -11,7 +11,8 @@ Stage 2, Stage 3).
            (double-float arithmetic on the fp32 pipes, fp64 I/O)
   plain    the same with native fp64 arithmetic (the plain partition solve)
   e2e      tps_solve_host_async from pinned host buffers: chunked H2D,
-           kernels and D2H on the plan's streams, all inside the timed region;
+           kernels and D2H on the plan's streams, all inside the timed region
+           (median of three rounds of steps);
            link_floor_ms is the same bytes moved as plain copies (H2D, then
            D2H) in the same run, the bound no pipeline can beat
            (e2e.zero_copy: the same through TPS_ZERO_COPY, kernels reading
@@ -536,15 +537,20 @@ def main():
         for _ in range(min(a.warmup, 3)):
             plan_h.solve_host_async(hk["a"], hk["b"], hk["c"], hk["d"], hx, stream=stream)
         stream.synchronize()
-        barrier(world)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(esteps):
-            plan_h.solve_host_async(hk["a"], hk["b"], hk["c"], hk["d"], hx, stream=stream)
-        e1.record(stream)
-        stream.synchronize()
-        barrier(world)
-        ems = max_over_ranks(e0.elapsed_time(e1) / esteps, world)
+        # three rounds of esteps solves; the host link is shared with the
+        # machine's other jobs, so the median round is reported (all are kept)
+        rounds = []
+        for _ in range(3):
+            barrier(world)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(esteps):
+                plan_h.solve_host_async(hk["a"], hk["b"], hk["c"], hk["d"], hx, stream=stream)
+            e1.record(stream)
+            stream.synchronize()
+            barrier(world)
+            rounds.append(max_over_ranks(e0.elapsed_time(e1) / esteps, world))
+        ems = statistics.median(rounds)
         infoh = plan_h.query()
         eh_err = (hx.to("cuda") - g["x_true"]).abs().max().item() / g["x_true"].abs().max().item()
         floor_ms = link_floor(hk, hx, g, x, stream)
@@ -607,7 +613,7 @@ def main():
                 "steps": esteps, "h2d_bytes_per_step": 4 * 8 * n, "d2h_bytes_per_step": 8 * n,
                 "streams": infoh["streams"], "chunk": infoh["chunk"],
                 "predicted": {"streams": pred_h["streams"], "chunk": pred_h["chunk"]},
-                "link_floor_ms": floor_ms, "frac_of_link_floor": floor_ms / ems,
+                "rounds_ms": rounds, "link_floor_ms": floor_ms, "frac_of_link_floor": floor_ms / ems,
                 "rel_fwd_vs_x_true": eh_err, "zero_copy": zc},
         "clocks": clocks,
     }

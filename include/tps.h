@@ -58,7 +58,9 @@ typedef enum {
                          /* iterative refinement to the plan's tolerance        */
   TPS_F64_DF = 3         /* fp64 I/O; double-float arithmetic (pairs of fp32)   */
                          /* on the fp32 pipes, about 2^-46 relative per op;     */
-                         /* for magnitudes in [2^-103, 2^127]                   */
+                         /* for magnitudes in [2^-103, 2^127]; a diagonal entry */
+                         /* beyond that range, infinite or NaN is reported as   */
+                         /* a pivot failure, in a, c, d it is not detected      */
 } tps_dtype;
 
 typedef enum {

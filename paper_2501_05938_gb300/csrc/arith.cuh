@@ -55,6 +55,7 @@ struct ArF64 {
     return ex == 0u || ex == 0x7FF00000u;
   }
   __device__ __forceinline__ static T from(double v) { return v; }
+  __device__ __forceinline__ static T from_pivot(double v) { return v; }
   __device__ __forceinline__ static T from(float v) { return (double)v; }
   __device__ __forceinline__ static void to(double& dst, T v) { dst = v; }
 };
@@ -78,13 +79,19 @@ struct ArF32 {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return fmaf(r, fmaf(-x, r, 1.0f), r);
   }
-  __device__ __forceinline__ static bool bad_pivot(T x) { return !(fabsf(x) >= 1.17549435e-38f); }
+  // zero, subnormal, infinite or NaN
+  __device__ __forceinline__ static bool bad_pivot(T x) {
+    const float m = fabsf(x);
+    return !(m >= 1.17549435e-38f && m <= 3.40282347e38f);
+  }
   __device__ __forceinline__ static T from(float v) { return v; }
   __device__ __forceinline__ static void to(float& dst, T v) { dst = v; }
   // fp64 storage (the fp32 elimination of the mixed-precision solve): the
   // value truncated to binary32 and widened back exactly, both with integer
   // operations (the conversion instructions run at the slow fp64 rate)
   __device__ __forceinline__ static T from(double v);
+  __device__ __forceinline__ static T from_pivot(float v) { return v; }
+  __device__ __forceinline__ static T from_pivot(double v);
   __device__ __forceinline__ static void to(double& dst, T v);
 };
 
@@ -126,6 +133,26 @@ __device__ __forceinline__ df64 df_split(double v) {
   return r;
 }
 
+// The same split for a value that feeds a pivot: magnitudes from 2^128 up,
+// infinities and NaN (whose exponent would wrap in df_split) have their
+// magnitude clamped to exponent 1151 with an all-ones significand first,
+// which gives a NaN high part that the pivot test reports (only finite
+// magnitudes in [2^128, 2^128 (1 + 2^-20)) come out infinite).  Two integer
+// operations more.
+__device__ __forceinline__ df64 df_split_checked(double v) {
+  const unsigned wl = (unsigned)__double2loint(v);
+  const unsigned wh = (unsigned)__double2hiint(v);
+  const bool ok = (wh & 0x7FF00000u) >= (920u << 20);
+  const unsigned whc = min(wh & 0x7FFFFFFFu, 0x47FFFFFFu);
+  const unsigned hb = (__funnelshift_l(wl, whc, 3) + 0x40000000u) | (wh & 0x80000000u);
+  const unsigned mag = (hb & 0xFF800000u) - 0x0B800000u;
+  const unsigned lob = mag | ((wl >> 6) & 0x007FFFFFu);
+  df64 r;
+  r.hi = ok ? __uint_as_float(hb) : 0.0f;
+  r.lo = ok ? __fsub_rn(__uint_as_float(lob), __uint_as_float(mag)) : 0.0f;
+  return r;
+}
+
 // Exact binary32 -> binary64 widening with integer operations (normal
 // floats and zero; subnormal floats come out slightly off, as if normal).
 __device__ __forceinline__ double f32_widen_bits(float f) {
@@ -137,6 +164,7 @@ __device__ __forceinline__ double f32_widen_bits(float f) {
 }
 
 __device__ __forceinline__ float ArF32::from(double v) { return df_split(v).hi; }
+__device__ __forceinline__ float ArF32::from_pivot(double v) { return df_split_checked(v).hi; }
 __device__ __forceinline__ void ArF32::to(double& dst, float v) { dst = f32_widen_bits(v); }
 
 struct ArDF {
@@ -231,9 +259,14 @@ struct ArDF {
     fast_two_sum(r, __fmul_rn(r, fmaf(e, e, e)), out.hi, out.lo);
     return out;
   }
+  // zero, subnormal or NaN high part (one comparison: non-finite inputs on
+  // the diagonal arrive here as NaN through df_split_checked)
   __device__ __forceinline__ static bool bad_pivot(T x) { return !(fabsf(x.hi) >= 1.17549435e-38f); }
   __device__ __forceinline__ static T from(double v) { return df_split(v); }
   __device__ __forceinline__ static T from(float2 v) { return {v.x, v.y}; }
+  // a diagonal entry: out-of-range inputs reach the pivot test
+  __device__ __forceinline__ static T from_pivot(double v) { return df_split_checked(v); }
+  __device__ __forceinline__ static T from_pivot(float2 v) { return from(v); }
   __device__ __forceinline__ static void to(double& dst, T v) {
     dst = __dadd_rn(f32_widen_bits(v.hi), f32_widen_bits(v.lo));
   }

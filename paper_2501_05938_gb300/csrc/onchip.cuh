@@ -71,7 +71,9 @@ struct AccL0 {
   using T = typename Ar::T;
   Tin* p[4];
   int r0;
-  __device__ __forceinline__ T ld(int k, int r) const { return Ar::from(p[k][r0 + r]); }
+  __device__ __forceinline__ T ld(int k, int r) const {
+    return k == 1 ? Ar::from_pivot(p[1][r0 + r]) : Ar::from(p[k][r0 + r]);  // b: checked
+  }
   __device__ __forceinline__ T rel(int k, int r) const {
     return *reinterpret_cast<const T*>(&p[k][r0 + r]);
   }

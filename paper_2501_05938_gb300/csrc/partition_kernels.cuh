@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(W * 32)
                          xc = lds16(t + 2 * TL::kArr + r), xd = lds16(t + 3 * TL::kArr + r);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-          interior(Ar::from(xa.v[v]), Ar::from(xb.v[v]), Ar::from(xc.v[v]), Ar::from(xd.v[v]));
+          interior(Ar::from(xa.v[v]), Ar::from_pivot(xb.v[v]), Ar::from(xc.v[v]), Ar::from(xd.v[v]));
           if constexpr (R > K) {  // chunk spans several checkpoint intervals
             if ((r + v + 1) % K == 0 && r + v + 1 < R) checkpoint(row0 + r + v);
           }
@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(W * 32)
         const int row = row0 + r;
         if (row < L) {
           T av = Ar::from(t[r]), cv = Ar::from(t[2 * TL::kArr + r]);
-          const T bv = Ar::from(t[TL::kArr + r]), dv = Ar::from(t[3 * TL::kArr + r]);
+          const T bv = Ar::from_pivot(t[TL::kArr + r]), dv = Ar::from(t[3 * TL::kArr + r]);
           if (bd.cnt > 0) {  // couplings cut at system boundaries
             if (bd.is(start + row)) av = Ar::zero();
             if (bd.is(start + row + 1)) cv = Ar::zero();

@@ -127,6 +127,43 @@ def test_zero_pivot_is_reported_not_raised():
         assert plan.query()["status"] == 0
 
 
+def test_workspace_allocation_failure_is_reported():
+    # a plan for 2^40 rows needs tens of TB of workspace: cudaMalloc fails, the plan
+    # reports TPS_ERR_OOM and nothing is left allocated
+    with pytest.raises(binding.TpsError) as ei:
+        binding.Plan(1 << 40, dtype="f64")
+    assert ei.value.status == 4
+    x, info = run(binding.Plan(1000, dtype="f64"), synth.system(1, 1000))  # still usable
+    assert info["status"] == 0
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f64_df", "f32"])
+@pytest.mark.parametrize("n", [1000, 100003, 1 << 21])
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
+def test_non_finite_diagonal_is_reported(dtype, n, bad):
+    s = synth.system(4, n)
+    tdt = torch.float64
+    if dtype == "f32":
+        s, tdt = synth.to_f32(s), torch.float32
+    s["b"][n // 3] = bad
+    _, info = run(binding.Plan(n, dtype=dtype), s, tdt)
+    assert info["status_name"] == "TPS_ERR_ZERO_PIVOT"
+
+
+@pytest.mark.parametrize("n", [1000, 1 << 21])
+def test_double_float_range_is_checked(n):
+    # 1e300 is a fine fp64 value but beyond the binary32 exponent range of
+    # the double-float arithmetic: reported, while the plain fp64 solve is exact
+    s = synth.system(6, n)
+    s["b"][n // 2] = 1e300
+    _, info = run(binding.Plan(n, dtype="f64_df"), s)
+    assert info["status_name"] == "TPS_ERR_ZERO_PIVOT"
+    x, info = run(binding.Plan(n, dtype="f64"), s)
+    assert info["status"] == 0
+    ref = oracle.thomas(s["a"], s["b"], s["c"], s["d"])
+    assert oracle.rel_forward_error(x, ref) <= F64_FWD
+
+
 def test_invalid_arguments():
     n = 1000
     plan = binding.Plan(n, dtype="f64")
