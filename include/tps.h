@@ -43,7 +43,7 @@ extern "C" {
 typedef enum {
   TPS_OK = 0,
   TPS_ERR_INVALID_ARG = 1,    /* bad pointer, size, alias, or plan misuse      */
-  TPS_ERR_UNSUPPORTED = 2,    /* valid request this build does not serve       */
+  TPS_ERR_UNSUPPORTED = 2,    /* valid request this library does not serve     */
   TPS_ERR_CUDA = 3,           /* a CUDA runtime call failed                    */
   TPS_ERR_OOM = 4,            /* device or pinned allocation failed            */
   TPS_ERR_ZERO_PIVOT = 5,     /* zero/non-finite pivot met (matrix not SDD)    */
