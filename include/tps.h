@@ -28,6 +28,11 @@
  *   come back as the return value, numeric errors (TPS_ERR_ZERO_PIVOT,
  *   TPS_ERR_NO_CONVERGENCE) from tps_plan_query after the stream has been
  *   synchronised.  A plan may be used by one stream at a time.
+ *   A plan belongs to the device that is current when tps_plan creates it:
+ *   every later call on it needs that device current, and its device
+ *   arrays on that device (or managed), else TPS_ERR_INVALID_ARG.  Distinct
+ *   plans may be used from different host threads at the same time; one
+ *   plan by one thread at a time.
  *   `stream` is a cudaStream_t passed as void* (NULL = legacy default).
  */
 #ifndef TPS_H
@@ -232,7 +237,9 @@ tps_status tps_solve_host_async(tps_plan_t plan, int64_t n, const void* a, const
  *   dtype       TPS_F64, TPS_F64_DF or TPS_F32 (as in tps_plan_desc)
  *   n           0 .. TPS_NOALLOC_MAX_ROWS; larger n gives TPS_ERR_INVALID_ARG
  *   a, b, c, d  device inputs, x device output (n elements of the I/O type;
- *               x must not overlap an input), owned by the caller
+ *               x must not overlap an input), owned by the caller, on the
+ *               current device; only alignment and overlap are checked (no
+ *               pointer queries on this path)
  *   status_out  optional device int32 that receives TPS_OK,
  *               TPS_ERR_ZERO_PIVOT or TPS_ERR_TIMEOUT when the solve has run
  *               (NULL: not reported)

@@ -27,7 +27,6 @@ constexpr int kM0 = 64;           // rows per block at the top level
 constexpr int kMr = 32;           // rows per block at the reduced levels
 constexpr int kMaxLevels = 8;
 constexpr size_t kScratchBytes = size_t(2) << 20;  // 2 MiB per GPU
-constexpr int kMaxDevices = 64;
 
 // The scratch array.  In host code `g_scratch` names a host-side shadow,
 // not device memory: its device address comes from cudaGetSymbolAddress.

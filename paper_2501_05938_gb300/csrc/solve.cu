@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 #include <vector>
 
@@ -42,30 +43,30 @@ static bool oc_geometry(int64_t n, int ctas_max, OcGeom& g) {
 
 // CTAs of k_onchip<Ar, Tin> that can be resident at once on the current
 // device (at most kOcMaxCtas), found once per device; 0 if it cannot run.
+// (Threads may race to fill an entry; they store the same value.)
 template <class Ar, class Tin>
 static int oc_ctas_max() {
-  static int cache[16] = {};
-  static bool have[16] = {};
+  static std::atomic<int> cache[kMaxDevices];  // CTAs + 1; 0 = not known yet
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) {
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
     return 0;
   }
-  if (!have[dev]) {
-    int sms = 0, per = 0;
-    const size_t smem = OcLayout<Ar, Tin>::kBytes;
-    if (cudaFuncSetAttribute(k_onchip<Ar, Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_onchip<Ar, Tin>, kOcThreads,
-                                                      smem) != cudaSuccess) {
-      cudaGetLastError();
-      per = 0;
-    }
-    cache[dev] = std::min(kOcMaxCtas, sms * per);
-    have[dev] = true;
+  const int known = cache[dev].load(std::memory_order_acquire);
+  if (known > 0) return known - 1;
+  int sms = 0, per = 0;
+  const size_t smem = OcLayout<Ar, Tin>::kBytes;
+  if (cudaFuncSetAttribute(k_onchip<Ar, Tin>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_onchip<Ar, Tin>, kOcThreads,
+                                                    smem) != cudaSuccess) {
+    cudaGetLastError();
+    per = 0;
   }
-  return cache[dev];
+  const int ctas = std::min(kOcMaxCtas, sms * per);
+  cache[dev].store(ctas + 1, std::memory_order_release);
+  return ctas;
 }
 
 // Solve the system on chip if it fits (used = true), else leave it.  xch:
@@ -181,12 +182,17 @@ static bool vec16_ok(int m, const void* const* ptrs, int n) {
   return true;
 }
 
+// The dynamic shared-memory limit is a per-device attribute of a kernel:
+// set it once per device (bit `dev` of `done`), from any host thread.
 template <class K>
-static cudaError_t set_smem(K kernel, size_t smem, bool& done) {
-  if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e == cudaSuccess) done = true;
+static cudaError_t set_smem(K kernel, size_t smem, std::atomic<uint64_t>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev < 64 ? (uint64_t(1) << dev) : 0;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_release);
   return e;
 }
 
@@ -208,12 +214,12 @@ static cudaError_t launch_stage1(const Level& lv, const Tin* a, const Tin* b, co
   const void* ptrs[4] = {a, b, c, d};
   cudaError_t e;
   if (vec16_ok<Tin>(lv.m, ptrs, 4)) {
-    static bool done = false;
+    static std::atomic<uint64_t> done{0};
     auto k = k_stage1<Ar, Tin, Tred, R, K, W, true>;
     if ((e = set_smem(k, smem, done)) != cudaSuccess) return e;
     k<<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, ra, rb, rc, rd, cg, cy, cv, status);
   } else {
-    static bool done = false;
+    static std::atomic<uint64_t> done{0};
     auto k = k_stage1<Ar, Tin, Tred, R, K, W, false>;
     if ((e = set_smem(k, smem, done)) != cudaSuccess) return e;
     k<<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, ra, rb, rc, rd, cg, cy, cv, status);
@@ -233,12 +239,12 @@ static cudaError_t launch_stage3(const Level& lv, const Tin* a, const Tin* b, co
   const void* ptrs[5] = {a, b, c, d, x};
   cudaError_t e;
   if (vec16_ok<Tin>(lv.m, ptrs, 5)) {
-    static bool done = false;
+    static std::atomic<uint64_t> done{0};
     auto k = k_stage3<Ar, Tin, Tred, R, W, true>;
     if ((e = set_smem(k, smem, done)) != cudaSuccess) return e;
     k<<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, xr, cg, cy, cv, x, status);
   } else {
-    static bool done = false;
+    static std::atomic<uint64_t> done{0};
     auto k = k_stage3<Ar, Tin, Tred, R, W, false>;
     if ((e = set_smem(k, smem, done)) != cudaSuccess) return e;
     k<<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, xr, cg, cy, cv, x, status);
@@ -551,7 +557,7 @@ static tps_status run_solve_direct(tps_plan_s* P, int64_t n, const void* a, cons
 template <class Ar, class Tin>
 static cudaError_t launch_window(tps_plan_s* P, int64_t n, const Tin* a, const Tin* b,
                                  const Tin* c, const Tin* d, Tin* x, cudaStream_t s) {
-  static bool done = false;  // the attribute allows the largest window
+  static std::atomic<uint64_t> done{0};  // the attribute allows the largest window
   cudaError_t e = set_smem(k_window<Ar, Tin>, WinLayout<Ar, Tin>::bytes(kWinRowsMax), done);
   if (e != cudaSuccess) return e;
   const int R = P->m, h = P->m_reduced;

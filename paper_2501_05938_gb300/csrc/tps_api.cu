@@ -149,9 +149,15 @@ tps_status tps_plan(const tps_plan_desc* desc, tps_plan_t* out) {
   }
   if ((d.flags & TPS_ZERO_COPY) && d.residency != TPS_HOST_PINNED) return TPS_ERR_INVALID_ARG;
 
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) {
+    cudaGetLastError();
+    return TPS_ERR_CUDA;
+  }
   tps_plan_s* P = new (std::nothrow) tps_plan_s();
   if (!P) return TPS_ERR_OOM;
   P->desc = d;
+  P->device = device;
   P->m = d.m;
   P->m_reduced = d.m_reduced;
   P->streams = d.streams;
@@ -290,12 +296,7 @@ tps_status tps_set_workspace(tps_plan_t P, void* dev_ptr, size_t bytes) {
   if (!P || !dev_ptr) return TPS_ERR_INVALID_ARG;
   if (!(P->desc.flags & TPS_EXTERNAL_WORKSPACE)) return TPS_ERR_INVALID_ARG;
   if (bytes < P->ws_needed || ((uintptr_t)dev_ptr % kAlign) != 0) return TPS_ERR_INVALID_ARG;
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, dev_ptr) != cudaSuccess ||
-      (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
-    cudaGetLastError();
-    return TPS_ERR_INVALID_ARG;
-  }
+  if (!on_plan_device(P) || !device_ptr_ok(dev_ptr, kAlign, P->device)) return TPS_ERR_INVALID_ARG;
   P->ws = (unsigned char*)dev_ptr;
   P->ws_bytes = bytes;
   P->ws_owned = false;
@@ -308,15 +309,27 @@ tps_status tps_set_workspace(tps_plan_t P, void* dev_ptr, size_t bytes) {
 
 namespace tps {
 
-// Device pointer check: device or managed memory, aligned to the element.
-static bool device_ptr_ok(const void* p, size_t align) {
+// Device pointer check: managed memory, or device memory of `device`,
+// aligned to `align` bytes.
+bool device_ptr_ok(const void* p, size_t align, int device) {
   if (!p || ((uintptr_t)p % align) != 0) return false;
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return at.type == cudaMemoryTypeManaged ||
+         (at.type == cudaMemoryTypeDevice && at.device == device);
+}
+
+// The plan's device is the current one.
+bool on_plan_device(const tps_plan_s* P) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return dev == P->device;
 }
 
 // Host pointer check: pinned host memory, or (pageable_ok: the device has
@@ -341,15 +354,18 @@ static tps_status check_solve_args(tps_plan_s* P, int64_t n, const void* a, cons
   if (!P) return TPS_ERR_INVALID_ARG;
   if (n < 0 || n > P->desc.n_max) return TPS_ERR_INVALID_ARG;
   if (!P->ws) return TPS_ERR_INVALID_ARG;  // external workspace not set
+  if (!on_plan_device(P)) return TPS_ERR_INVALID_ARG;
   if (n == 0) return TPS_OK;
   const size_t es = elem_bytes_io(P->desc.dtype);
   const void* in[4] = {a, b, c, d};
   const bool pageable = host && (P->desc.flags & TPS_ZERO_COPY) && P->pageable_ok;
   for (const void* p : in) {
-    if (host ? !host_ptr_ok(p, es, pageable) : !device_ptr_ok(p, es)) return TPS_ERR_INVALID_ARG;
+    if (host ? !host_ptr_ok(p, es, pageable) : !device_ptr_ok(p, es, P->device))
+      return TPS_ERR_INVALID_ARG;
     if (overlaps(p, x, (size_t)n * es)) return TPS_ERR_INVALID_ARG;
   }
-  if (host ? !host_ptr_ok(x, es, pageable) : !device_ptr_ok(x, es)) return TPS_ERR_INVALID_ARG;
+  if (host ? !host_ptr_ok(x, es, pageable) : !device_ptr_ok(x, es, P->device))
+    return TPS_ERR_INVALID_ARG;
   return TPS_OK;
 }
 
@@ -381,7 +397,7 @@ tps_status tps_solve_batched(tps_plan_t P, int64_t count, const int64_t* offsets
   if (count > P->desc.batch_max) return TPS_ERR_INVALID_ARG;
   if (P->desc.flags & TPS_TRUNCATE) return TPS_ERR_UNSUPPORTED;
   if (count == 0) return TPS_OK;
-  if ((uintptr_t)offsets % 8) return TPS_ERR_INVALID_ARG;
+  if (!on_plan_device(P) || !device_ptr_ok(offsets, 8, P->device)) return TPS_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   int64_t n = 0;
   if (host_offsets) {

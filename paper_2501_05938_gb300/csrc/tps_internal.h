@@ -26,6 +26,8 @@ constexpr int kChunkRows = sizeof(T) >= 8 ? TPS_CHUNK_ROWS_8B : 16;
 #define TPS_WARPS_PER_CTA 1
 #endif
 constexpr int kWarpsPerCta = TPS_WARPS_PER_CTA;
+// devices a process may use (per-device caches of kernel attributes)
+constexpr int kMaxDevices = 64;
 
 // One level of the recursive solve: the system at this level has lv.n rows
 // and is split into lv.p blocks; its reduced system (2 lv.p rows) and the
@@ -40,6 +42,11 @@ struct LevelPlan {
 // Block geometry for n rows and nominal block length m (m >= 2, n > m is
 // not required): p = ceil(n/m) blocks, a one-row tail merged into the block
 // before it so every block has >= 2 rows.
+// Argument checks shared by the entry points: managed memory or device
+// memory of `device`, aligned to `align`; the plan's device is current.
+bool device_ptr_ok(const void* p, size_t align, int device);
+bool on_plan_device(const tps_plan_s* P);
+
 Level make_level(int64_t n, int m, int R);
 
 // Levels of the recursive solve of an n-row system (empty when n fits the
@@ -54,6 +61,7 @@ struct HostPipe;  // streams and events of tps_solve_host_async
 
 struct tps_plan_s {
   tps_plan_desc desc;
+  int32_t device = -1;  // the device current at tps_plan; every call must use it
   int32_t m = 0, m_reduced = 0, streams = 1;
   int64_t chunk = 0;
   unsigned char* ws = nullptr;

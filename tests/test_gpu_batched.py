@@ -86,6 +86,9 @@ def test_batch_argument_checks():
     with pytest.raises(binding.TpsError):  # decreasing offsets
         plan.solve_batched(offs[:3], z, z, z, z, torch.zeros_like(z),
                            host_offsets=np.array([0, 60, 50]))
+    with pytest.raises(binding.TpsError):  # offsets the kernels read must be device memory
+        plan.solve_batched(torch.as_tensor(np.array([0, 50, 100])), z, z, z, z,
+                           torch.zeros_like(z), host_offsets=np.array([0, 50, 100]))
 
 
 @pytest.mark.slow

@@ -192,6 +192,10 @@ def test_external_workspace():
     s = synth.system(8, n)
     plan = binding.Plan(n, dtype="f64_df", m=32, flags=binding.EXTERNAL_WORKSPACE)
     need = plan.workspace_size()
+    with pytest.raises(binding.TpsError):  # the workspace must be device memory
+        plan.set_workspace(torch.empty(need, dtype=torch.uint8, pin_memory=True))
+    with pytest.raises(binding.TpsError):  # and large enough
+        plan.set_workspace(torch.empty(need - 256, dtype=torch.uint8, device="cuda"))
     ws = torch.empty(need, dtype=torch.uint8, device="cuda")
     plan.set_workspace(ws)
     x, info = run(plan, s)
