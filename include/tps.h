@@ -170,6 +170,12 @@ tps_status tps_set_workspace(tps_plan_t plan, void* dev_ptr, size_t bytes);
  * every CTA solves the small system of CTA interface rows, and recovers its
  * rows on chip.  The reduced system of a larger solve takes the same path
  * once it fits.  TPS_NO_ONCHIP keeps every level on separate launches.
+ * The grid barrier waits a bounded time: if the launch's CTAs cannot all
+ * become resident (another such launch from another stream, or other
+ * long-running work holding the SMs), the wait ends, the solve reports
+ * TPS_ERR_TIMEOUT through tps_plan_query and the context stays usable; run
+ * on-chip solves of different streams one after the other, or use
+ * TPS_NO_ONCHIP for plans that run concurrently.
  *
  * TPS_TRUNCATE (device plans, fp64 / double-float / fp32; not the paper's
  * method, an approximation for strongly dominant systems): windows of m kept

@@ -139,18 +139,41 @@ class Plan:
         check(lib().tps_set_workspace(self._h, _ptr(buf), buf.numel() * buf.element_size()),
               "tps_set_workspace")
 
+    def _arrays(self, n, *ts):
+        """a, b, c, d, x: contiguous tensors of the plan's I/O type (float32
+        for "f32", float64 otherwise), n elements each (the library checks
+        where they live)."""
+        import torch
+
+        want = torch.float32 if self.dtype == "f32" else torch.float64
+        for t in ts:
+            if t.dtype != want or not t.is_contiguous() or t.numel() != n:
+                raise TpsError(1, f"arrays must be contiguous {want} tensors of {n} elements")
+
+    @staticmethod
+    def _offsets(offsets, host_offsets):
+        import numpy as np
+        import torch
+
+        if offsets is not None and (offsets.dtype != torch.int64 or not offsets.is_contiguous()):
+            raise TpsError(1, "offsets must be a contiguous int64 tensor")
+        if host_offsets is None:
+            return None, None
+        h = np.ascontiguousarray(host_offsets, dtype=np.int64)
+        return h, ctypes.c_void_p(h.ctypes.data)
+
     def solve(self, a, b, c, d, x, stream=None):
         """Device-resident solve; a..x are CUDA tensors of n elements."""
         n = b.numel()
+        self._arrays(n, a, b, c, d, x)
         check(lib().tps_solve(self._h, n, _ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(x),
                               _stream(stream)), "tps_solve")
         return x
 
     def solve_batched(self, offsets, a, b, c, d, x, host_offsets=None, stream=None):
         count = offsets.numel() - 1
-        hp = None
-        if host_offsets is not None:
-            hp = ctypes.c_void_p(host_offsets.ctypes.data)
+        self._arrays(b.numel(), a, b, c, d, x)
+        keep, hp = self._offsets(offsets, host_offsets)  # keep: alive during the call
         check(lib().tps_solve_batched(self._h, count, _ptr(offsets), hp, _ptr(a), _ptr(b),
                                       _ptr(c), _ptr(d), _ptr(x), _stream(stream)),
               "tps_solve_batched")
@@ -160,6 +183,7 @@ class Plan:
         """a..x are pinned CPU tensors (ZERO_COPY plans: or pageable ones where
         the device reads pageable memory); returns after enqueueing."""
         n = b.numel()
+        self._arrays(n, a, b, c, d, x)
         check(lib().tps_solve_host_async(self._h, n, _ptr(a), _ptr(b), _ptr(c), _ptr(d),
                                          _ptr(x), _stream(stream)), "tps_solve_host_async")
         return x
@@ -176,7 +200,8 @@ class Plan:
         L.tps_autotune.restype = ctypes.c_int
         m, ms = ctypes.c_int32(), ctypes.c_float()
         count = 0 if offsets is None else offsets.numel() - 1
-        hp = None if host_offsets is None else ctypes.c_void_p(host_offsets.ctypes.data)
+        self._arrays(b.numel(), a, b, c, d, x)
+        keep, hp = self._offsets(offsets, host_offsets)  # keep: alive during the call
         check(L.tps_autotune(self._h, b.numel(), count, _ptr(offsets), hp, _ptr(a), _ptr(b),
                              _ptr(c), _ptr(d), _ptr(x), _stream(stream), int(reps),
                              ctypes.byref(m), ctypes.byref(ms)), "tps_autotune")

@@ -424,3 +424,41 @@ def test_graph_mode_batched():
         torch.cuda.synchronize()
         ref = oracle.thomas_batched(off, s["a"], s["b"], s["c"], s["d"])
         assert oracle.rel_forward_error(x.cpu().numpy(), ref) <= F64_FWD
+
+
+def test_distinct_plans_from_two_host_threads():
+    # two host threads, each with its own plan and stream, solving at the
+    # same time (levels route: no cooperative launch), both against the oracle
+    import threading
+
+    n = 300001
+    systems = [synth.system(60 + i, n) for i in range(2)]
+    refs = [oracle.thomas(s["a"], s["b"], s["c"], s["d"]) for s in systems]
+    out, errs = [None, None], []
+
+    def work(i):
+        try:
+            torch.cuda.set_device(0)
+            st = torch.cuda.Stream()
+            with torch.cuda.stream(st):
+                a, b, c, d = (dev(systems[i][k]) for k in "abcd")
+                x = torch.empty_like(b)
+                plan = binding.Plan(n, dtype=("f64_df", "f64")[i], m=64 * (i + 1),
+                                    flags=binding.NO_ONCHIP | binding.GRAPH * i)
+                for _ in range(25):
+                    plan.solve(a, b, c, d, x)
+            st.synchronize()
+            out[i] = (x.cpu().numpy(), plan.query())
+        except Exception as e:  # surfaced below
+            errs.append(e)
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errs, errs
+    for (x, info), ref, s in zip(out, refs, systems):
+        assert info["status"] == 0 and info["onchip"] == 0
+        assert oracle.rel_forward_error(x, ref) <= F64_FWD
+        assert oracle.rel_residual(s["a"], s["b"], s["c"], s["d"], x) <= F64_RES
