@@ -83,6 +83,8 @@ typedef enum {
                                   /* move host data (see tps_solve_host_async)    */
 #define TPS_NO_ONCHIP 64u         /* never use the single-launch on-chip solve    */
 #define TPS_TRUNCATE 128u         /* approximate windowed solve (see tps_solve)   */
+#define TPS_HOST_OVERLAP 256u     /* host residency: a second buffer set so that  */
+                                  /* tps_solve_host_many_async overlaps systems   */
 
 typedef struct {
   int64_t n_max;     /* largest n of tps_solve / tps_solve_host_async, or the  */
@@ -227,6 +229,33 @@ tps_status tps_solve_batched(tps_plan_t plan, int64_t count, const int64_t* offs
  * completes.  mixed dtype: TPS_ERR_UNSUPPORTED. */
 tps_status tps_solve_host_async(tps_plan_t plan, int64_t n, const void* a, const void* b,
                                 const void* c, const void* d, void* x, void* stream);
+
+/* Solve `count` independent host-resident systems of n rows each, in order,
+ * overlapping consecutive systems: each system runs the pipeline of
+ * tps_solve_host_async, and consecutive systems alternate between two sets
+ * of device buffers, workspaces and S streams (the plan's own and those of
+ * a twin plan that tps_plan makes for TPS_HOST_OVERLAP), so system k+1
+ * uploads while system k finishes Stage 3 and downloads: the link carries
+ * both directions at once.  One system alone cannot do this, since none of
+ * its x can leave before all of its rows have arrived (Stage 2 couples
+ * them).
+ *   plan        made with residency TPS_HOST_PINNED and TPS_HOST_OVERLAP
+ *               (which implies TPS_NO_ONCHIP: two on-chip cooperative launches
+ *               of different systems may not run at once; not with
+ *               TPS_EXTERNAL_WORKSPACE); the twin follows the plan's m,
+ *               m_reduced, S and chunk, including tps_autotune's choice
+ *   n           rows of every system, 0 .. n_max
+ *   a, b, c, d  count host pointers each (inputs, as for
+ *               tps_solve_host_async); systems may share inputs
+ *   x           count host pointers (outputs); x[k] must not overlap x[k+1]
+ *               or any input of systems k-1, k, k+1 (TPS_ERR_INVALID_ARG)
+ * Stream-ordered on `stream` as one operation (it starts after the work
+ * already in `stream`, and `stream` waits for every system); returns after
+ * enqueueing.  Numeric status of all systems: tps_plan_query on the plan. */
+tps_status tps_solve_host_many_async(tps_plan_t plan, int64_t count, int64_t n,
+                                     const void* const* a, const void* const* b,
+                                     const void* const* c, const void* const* d,
+                                     void* const* x, void* stream);
 
 /* Largest system tps_solve_noalloc accepts, in rows. */
 #define TPS_NOALLOC_MAX_ROWS 262144

@@ -21,11 +21,12 @@ RESIDENCY = {"device": 0, "host": 1}
 TUNE_PREDICT, TUNE_EXHAUSTIVE, TRACE, EXTERNAL_WORKSPACE, GRAPH, ZERO_COPY, NO_ONCHIP = (
     1, 2, 4, 8, 16, 32, 64)
 TRUNCATE = 128
+HOST_OVERLAP = 256
 
 # every symbol include/tps.h declares
 EXPORTS = ("tps_plan", "tps_plan_destroy", "tps_workspace_size", "tps_set_workspace", "tps_solve",
-           "tps_solve_batched", "tps_solve_host_async", "tps_plan_query", "tps_status_string",
-           "tps_version")
+           "tps_solve_batched", "tps_solve_host_async", "tps_solve_host_many_async",
+           "tps_plan_query", "tps_status_string", "tps_version")
 
 
 class PlanDesc(ctypes.Structure):
@@ -71,6 +72,8 @@ def lib():
         L.tps_solve.argtypes = [P, I64, P, P, P, P, P, P]
         L.tps_solve_batched.argtypes = [P, I64, P, P, P, P, P, P, P, P]
         L.tps_solve_host_async.argtypes = [P, I64, P, P, P, P, P, P]
+        PP = ctypes.POINTER(P)
+        L.tps_solve_host_many_async.argtypes = [P, I64, I64, PP, PP, PP, PP, PP, P]
         L.tps_plan_query.argtypes = [P, ctypes.POINTER(Info)]
         L.tps_status_string.argtypes = [I32]
         L.tps_status_string.restype = ctypes.c_char_p
@@ -187,6 +190,24 @@ class Plan:
         check(lib().tps_solve_host_async(self._h, n, _ptr(a), _ptr(b), _ptr(c), _ptr(d),
                                          _ptr(x), _stream(stream)), "tps_solve_host_async")
         return x
+
+    def solve_host_many(self, systems, xs, stream=None):
+        """tps_solve_host_many_async (plans made with HOST_OVERLAP): systems is
+        a list of (a, b, c, d) pinned CPU tensors of n elements, xs the list of
+        outputs; consecutive systems overlap on the link.  Returns after
+        enqueueing."""
+        count = len(systems)
+        if len(xs) != count:
+            raise TpsError(1, "one output per system")
+        n = systems[0][1].numel() if count else 0
+        for (a, b, c, d), x in zip(systems, xs):
+            self._arrays(n, a, b, c, d, x)
+        lists = [(ctypes.c_void_p * max(count, 1))(*[t.data_ptr() for t in col])
+                 for col in ([s[i] for s in systems] for i in range(4))]
+        xl = (ctypes.c_void_p * max(count, 1))(*[t.data_ptr() for t in xs])
+        check(lib().tps_solve_host_many_async(self._h, count, n, *lists, xl, _stream(stream)),
+              "tps_solve_host_many_async")
+        return xs
 
     def autotune(self, a, b, c, d, x, reps=3, offsets=None, host_offsets=None, stream=None):
         """tps_autotune: time every block size on these arrays and keep the

@@ -138,8 +138,13 @@ tps_status tps_plan(const tps_plan_desc* desc, tps_plan_t* out) {
   if (d.streams != 0 && (d.streams < 1 || d.streams > 32)) return TPS_ERR_INVALID_ARG;
   if (d.chunk < 0 || d.max_iters < 0 || d.tol < 0.0) return TPS_ERR_INVALID_ARG;
   if (d.flags & ~(TPS_TUNE_PREDICT | TPS_TUNE_EXHAUSTIVE | TPS_TRACE | TPS_EXTERNAL_WORKSPACE |
-                  TPS_GRAPH | TPS_ZERO_COPY | TPS_NO_ONCHIP | TPS_TRUNCATE))
+                  TPS_GRAPH | TPS_ZERO_COPY | TPS_NO_ONCHIP | TPS_TRUNCATE | TPS_HOST_OVERLAP))
     return TPS_ERR_INVALID_ARG;
+  if (d.flags & TPS_HOST_OVERLAP) {
+    if (d.residency != TPS_HOST_PINNED) return TPS_ERR_INVALID_ARG;
+    if ((d.flags & TPS_EXTERNAL_WORKSPACE) || d.dtype == TPS_MIXED_F32_F64)
+      return TPS_ERR_UNSUPPORTED;
+  }
   if (d.flags & TPS_TRUNCATE) {
     // windows of m kept rows and m_reduced halo rows (both even, 0 = choose)
     if (d.residency != TPS_DEVICE || d.dtype == TPS_MIXED_F32_F64) return TPS_ERR_UNSUPPORTED;
@@ -157,6 +162,7 @@ tps_status tps_plan(const tps_plan_desc* desc, tps_plan_t* out) {
   tps_plan_s* P = new (std::nothrow) tps_plan_s();
   if (!P) return TPS_ERR_OOM;
   P->desc = d;
+  if (d.flags & TPS_HOST_OVERLAP) P->desc.flags |= TPS_NO_ONCHIP;
   P->device = device;
   P->m = d.m;
   P->m_reduced = d.m_reduced;
@@ -257,6 +263,31 @@ tps_status tps_plan(const tps_plan_desc* desc, tps_plan_t* out) {
       return TPS_ERR_CUDA;
     }
   }
+  if (d.flags & TPS_HOST_OVERLAP) {
+    // the twin: the same plan with the parameters chosen above, fixed
+    tps_plan_desc t = P->desc;
+    t.flags &= ~(TPS_HOST_OVERLAP | TPS_TUNE_PREDICT | TPS_TUNE_EXHAUSTIVE | TPS_TRACE);
+    t.m = P->m;
+    t.m_reduced = P->m_reduced;
+    t.streams = P->streams;
+    t.chunk = P->chunk;
+    tps_status ts = tps_plan(&t, &P->twin);
+    if (ts != TPS_OK) {
+      P->twin = nullptr;
+      tps_plan_destroy(P);
+      return ts;
+    }
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+      e = cudaStreamCreateWithFlags(&P->lane[i], cudaStreamNonBlocking);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+      e = cudaEventCreateWithFlags(&P->lane_ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      tps_plan_destroy(P);
+      return TPS_ERR_CUDA;
+    }
+  }
   *out = P;
   return TPS_OK;
 }
@@ -277,6 +308,11 @@ tps_status tps_plan_destroy(tps_plan_t P) {
       if (P->trace_ev[i]) cudaEventDestroy(P->trace_ev[i]);
     delete[] P->trace_ev;
   }
+  if (P->twin) tps_plan_destroy(P->twin);
+  for (auto s : P->lane)
+    if (s) cudaStreamDestroy(s);
+  for (auto e : P->lane_ev)
+    if (e) cudaEventDestroy(e);
   if (P->graph) cudaGraphExecDestroy(P->graph);
   if (P->solve_graph) cudaGraphExecDestroy(P->solve_graph);
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
@@ -527,6 +563,52 @@ tps_status tps_solve_host_async(tps_plan_t P, int64_t n, const void* a, const vo
   return e == cudaSuccess ? TPS_OK : TPS_ERR_CUDA;
 }
 
+tps_status tps_solve_host_many_async(tps_plan_t P, int64_t count, int64_t n,
+                                     const void* const* a, const void* const* b,
+                                     const void* const* c, const void* const* d,
+                                     void* const* x, void* stream) {
+  if (!P || !P->twin || count < 0) return TPS_ERR_INVALID_ARG;
+  if (count > 0 && (!a || !b || !c || !d || !x)) return TPS_ERR_INVALID_ARG;
+  if (n < 0 || n > P->desc.n_max || !on_plan_device(P)) return TPS_ERR_INVALID_ARG;
+  if (count == 0 || n == 0) return TPS_OK;
+  // systems k and k+1 run at the same time: an output may not overlap the
+  // other one's output or inputs (each call checks its own arrays)
+  const size_t bytes = (size_t)n * elem_bytes_io(P->desc.dtype);
+  for (int64_t k = 0; k + 1 < count; ++k) {
+    const void* in0[4] = {a[k], b[k], c[k], d[k]};
+    const void* in1[4] = {a[k + 1], b[k + 1], c[k + 1], d[k + 1]};
+    if (overlaps(x[k], x[k + 1], bytes)) return TPS_ERR_INVALID_ARG;
+    for (int i = 0; i < 4; ++i)
+      if (overlaps(x[k], in1[i], bytes) || overlaps(x[k + 1], in0[i], bytes))
+        return TPS_ERR_INVALID_ARG;
+  }
+  tps_plan_s* T = P->twin;  // follows the plan's (possibly autotuned) parameters
+  T->m = P->m;
+  T->m_reduced = P->m_reduced;
+  T->streams = P->streams;
+  T->chunk = P->chunk;
+  cudaStream_t us = (cudaStream_t)stream;
+  cudaError_t e = ensure_streams(T->pipe, T->streams);
+  if (e == cudaSuccess) e = cudaEventRecord(P->lane_ev[0], us);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(P->lane[i], P->lane_ev[0], 0);
+  if (e != cudaSuccess) return TPS_ERR_CUDA;
+  tps_status st = TPS_OK;
+  for (int64_t k = 0; k < count && st == TPS_OK; ++k) {
+    tps_plan_s* Q = (k & 1) ? T : P;
+    st = tps_solve_host_async(Q, n, a[k], b[k], c[k], d[k], x[k], P->lane[k & 1]);
+  }
+  // join both buffer sets back into the caller's stream, also after an error
+  // (the systems already enqueued stay ordered before later work)
+  e = cudaEventRecord(P->lane_ev[1], P->lane[0]);
+  if (e == cudaSuccess) e = cudaEventRecord(P->lane_ev[2], P->lane[1]);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(us, P->lane_ev[1], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(us, P->lane_ev[2], 0);
+  P->last_stream = us;
+  T->last_stream = us;
+  if (st != TPS_OK) return st;
+  return e == cudaSuccess ? TPS_OK : TPS_ERR_CUDA;
+}
+
 }  // extern "C"
 
 namespace tps {
@@ -682,6 +764,14 @@ tps_status tps_plan_query(tps_plan_t P, tps_info* out) {
   if (cudaMemcpy(&word, P->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
     return TPS_ERR_CUDA;
   if (cudaMemset(P->d_status, 0, sizeof(int)) != cudaSuccess) return TPS_ERR_CUDA;
+  if (P->twin && P->twin->ws) {  // the systems the twin solved
+    int tw = 0;
+    if (cudaStreamSynchronize(P->twin->last_stream) != cudaSuccess ||
+        cudaMemcpy(&tw, P->twin->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(P->twin->d_status, 0, sizeof(int)) != cudaSuccess)
+      return TPS_ERR_CUDA;
+    word |= tw;
+  }
   int32_t status = TPS_OK;
   if (word & ST_BAD_PIVOT) status = TPS_ERR_ZERO_PIVOT;
   else if (word & ST_TIMEOUT) status = TPS_ERR_TIMEOUT;

@@ -107,6 +107,13 @@ struct tps_plan_s {
   // batched work list (device) and its capacity in entries
   void* d_work = nullptr;
   size_t work_cap = 0;
+  // TPS_HOST_OVERLAP: the twin plan (second buffer set and streams) that
+  // takes every other system of tps_solve_host_many_async, one stream per
+  // buffer set through which that set's systems are ordered, and events to
+  // fork from and join back into the caller's stream
+  tps_plan_s* twin = nullptr;
+  cudaStream_t lane[2] = {nullptr, nullptr};
+  cudaEvent_t lane_ev[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace tps {

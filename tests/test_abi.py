@@ -65,8 +65,11 @@ def test_plan_rejects_bad_descriptors_on_the_host(lib, field, value):
     ({"flags": 128, "residency": 1}, 2),               # truncation is device-resident only
     ({"flags": 128, "dtype": 2}, 2),                   # and not for the refinement dtype
     ({"flags": 32 | 128, "residency": 1}, 2),
+    ({"flags": 256}, 1),                               # overlap needs host residency
+    ({"flags": 256 | 8, "residency": 1}, 2),           # and its own workspaces
+    ({"flags": 256, "residency": 1, "dtype": 2}, 2),
 ])
-def test_truncate_descriptor_checks_on_the_host(lib, fields, status):
+def test_descriptor_flag_checks_on_the_host(lib, fields, status):
     d = binding.PlanDesc(n_max=1000, dtype=0)
     for k, v in fields.items():
         setattr(d, k, v)
@@ -79,7 +82,8 @@ def test_flag_constants_match_the_header():
     hdr = open(os.path.join(ROOT, "include", "tps.h")).read()
     for name, val in (("TPS_GRAPH", binding.GRAPH), ("TPS_ZERO_COPY", binding.ZERO_COPY),
                       ("TPS_NO_ONCHIP", binding.NO_ONCHIP), ("TPS_TRUNCATE", binding.TRUNCATE),
-                      ("TPS_TRACE", binding.TRACE), ("TPS_TUNE_PREDICT", binding.TUNE_PREDICT)):
+                      ("TPS_TRACE", binding.TRACE), ("TPS_TUNE_PREDICT", binding.TUNE_PREDICT),
+                      ("TPS_HOST_OVERLAP", binding.HOST_OVERLAP)):
         m = re.search(r"#define\s+" + name + r"\s+(\d+)u", hdr)
         assert m and int(m.group(1)) == val, name
 
@@ -90,6 +94,7 @@ def test_null_arguments(lib):
     assert lib.tps_plan_destroy(None) == 1
     assert lib.tps_solve(None, 10, None, None, None, None, None, None) == 1
     assert lib.tps_solve_host_async(None, 10, None, None, None, None, None, None) == 1
+    assert lib.tps_solve_host_many_async(None, 2, 10, None, None, None, None, None, None) == 1
     assert lib.tps_plan_query(None, None) == 1
     sz = ctypes.c_size_t()
     assert lib.tps_workspace_size(None, ctypes.byref(sz)) == 1

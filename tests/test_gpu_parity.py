@@ -267,6 +267,79 @@ def test_host_autotune_keeps_a_working_stream_and_chunk_choice(flags):
     assert oracle.rel_forward_error(x.numpy(), ref) <= F64_FWD
 
 
+def host_systems(dtype, n, seeds):
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    systems, refs = [], []
+    for seed in seeds:
+        s = synth.system(seed, n)
+        if dtype == "f32":
+            s = synth.to_f32(s)
+        systems.append(tuple(torch.as_tensor(np.ascontiguousarray(s[k])).to(tdt).pin_memory()
+                             for k in "abcd"))
+        a, b, c, d = (np.asarray(s[k], dtype=np.float64) for k in "abcd")
+        refs.append(oracle.thomas(a, b, c, d))
+    return systems, refs, tdt
+
+
+@pytest.mark.parametrize("dtype,S,flags", [("f64_df", 2, 0), ("f64", 4, binding.GRAPH),
+                                           ("f32", 2, binding.ZERO_COPY)])
+def test_host_many_overlaps_systems_and_matches_oracle(dtype, S, flags):
+    n, count = 300001, 5
+    systems, refs, tdt = host_systems(dtype, n, [500 + k for k in range(count)])
+    xs = [torch.full((n,), float("nan"), dtype=tdt).pin_memory() for _ in range(count)]
+    plan = binding.Plan(n, dtype=dtype, residency="host", streams=S, chunk=1 << 16,
+                        flags=binding.HOST_OVERLAP | flags)
+    plan.solve_host_many(systems, xs)
+    torch.cuda.synchronize()
+    info = plan.query()
+    assert info["status"] == 0 and info["onchip"] == 0
+    tol = F32_FWD if dtype == "f32" else F64_FWD
+    for x, ref in zip(xs, refs):
+        assert oracle.rel_forward_error(x.numpy().astype(np.float64), ref) <= tol
+    # after tps_autotune changes S and chunk, the twin follows
+    a, b, c, d = systems[0]
+    plan.autotune(a, b, c, d, xs[0], reps=1)
+    for x in xs:
+        x.fill_(float("nan"))
+    plan.solve_host_many(systems, xs)
+    torch.cuda.synchronize()
+    assert plan.query()["status"] == 0
+    for x, ref in zip(xs, refs):
+        assert oracle.rel_forward_error(x.numpy().astype(np.float64), ref) <= tol
+
+
+def test_host_many_reports_the_twins_systems_and_checks_outputs():
+    n = 100003
+    systems, refs, tdt = host_systems("f64_df", n, [71, 72, 71])
+    plan = binding.Plan(n, dtype="f64_df", residency="host", streams=2,
+                        flags=binding.HOST_OVERLAP)
+    # outputs of systems two apart may be the same buffer
+    x0, x1 = (torch.empty(n, dtype=tdt).pin_memory() for _ in range(2))
+    plan.solve_host_many(systems, [x0, x1, x0])
+    torch.cuda.synchronize()
+    assert plan.query()["status"] == 0
+    assert oracle.rel_forward_error(x0.numpy(), refs[2]) <= F64_FWD
+    assert oracle.rel_forward_error(x1.numpy(), refs[1]) <= F64_FWD
+    # a non-finite pivot in system 1 (solved by the twin) reaches the plan's status
+    bad = list(systems[1])
+    bad[1] = bad[1].clone().pin_memory()
+    bad[1][n // 2] = float("nan")
+    plan.solve_host_many([systems[0], tuple(bad)], [x0, x1])
+    torch.cuda.synchronize()
+    assert plan.query()["status_name"] == "TPS_ERR_ZERO_PIVOT"
+    assert plan.query()["status"] == 0  # the query resets both status words
+    with pytest.raises(binding.TpsError):  # consecutive outputs overlap
+        plan.solve_host_many(systems[:2], [x0, x0])
+    with pytest.raises(binding.TpsError):  # an output overlaps the next system's input
+        plan.solve_host_many(systems[:2], [systems[1][3], x1])
+    plain = binding.Plan(n, dtype="f64_df", residency="host", streams=2)
+    with pytest.raises(binding.TpsError):  # the plan has no twin
+        plain.solve_host_many(systems[:2], [x0, x1])
+    with pytest.raises(binding.TpsError):  # overlap is for host residency
+        binding.Plan(n, dtype="f64_df", flags=binding.HOST_OVERLAP)
+    plan.solve_host_many([], [])  # nothing to do
+
+
 def test_host_pipeline_rejects_pageable_and_device_memory():
     n = 1000
     plan = binding.Plan(n, dtype="f64", residency="host", streams=2)
