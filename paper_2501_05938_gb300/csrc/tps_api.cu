@@ -21,6 +21,7 @@ struct HostPipe {
   std::vector<cudaEvent_t> ev_done3;   // per stream: its Stage-3 work is queued
   cudaEvent_t ev_start = nullptr;      // caller's stream reached the solve
   cudaEvent_t ev_red = nullptr;        // Stage 2 done
+  cudaEvent_t ev_up = nullptr;         // every upload (and Stage 1) done
   size_t off_dev = 0;                  // device working copies a, b, c, d, x
 };
 
@@ -227,6 +228,7 @@ tps_status tps_plan(const tps_plan_desc* desc, tps_plan_t* out) {
     H->off_dev = off_dev;
     cudaError_t e = cudaEventCreateWithFlags(&H->ev_start, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&H->ev_red, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&H->ev_up, cudaEventDisableTiming);
     if (e == cudaSuccess) e = ensure_streams(H, P->streams);
     if (e != cudaSuccess) {
       tps_plan_destroy(P);
@@ -301,6 +303,7 @@ tps_status tps_plan_destroy(tps_plan_t P) {
     for (auto e : H->ev_done3) cudaEventDestroy(e);
     if (H->ev_start) cudaEventDestroy(H->ev_start);
     if (H->ev_red) cudaEventDestroy(H->ev_red);
+    if (H->ev_up) cudaEventDestroy(H->ev_up);
     delete H;
   }
   if (P->trace_ev) {
@@ -504,6 +507,7 @@ tps_status tps_solve_host_async(tps_plan_t P, int64_t n, const void* a, const vo
     cudaStream_t s0 = H->streams[0];
     for (int i = 0; i < 4 && e == cudaSuccess; ++i)
       e = copy(dev[i], host[i], (size_t)n * es, cudaMemcpyHostToDevice, s0);
+    if (e == cudaSuccess) e = cudaEventRecord(H->ev_up, s0);
     if (e == cudaSuccess) e = base_solve(P, n, dev[0], dev[1], dev[2], dev[3], dev[4], s0);
     if (e == cudaSuccess)
       e = copy((void*)host[4], dev[4], (size_t)n * es, cudaMemcpyDeviceToHost, s0);
@@ -540,6 +544,7 @@ tps_status tps_solve_host_async(tps_plan_t P, int64_t n, const void* a, const vo
     e = cudaEventRecord(H->ev_done1[i], H->streams[i]);
     if (e == cudaSuccess && i > 0) e = cudaStreamWaitEvent(H->streams[0], H->ev_done1[i], 0);
   }
+  if (e == cudaSuccess) e = cudaEventRecord(H->ev_up, H->streams[0]);
   if (e == cudaSuccess)
     e = (P->desc.flags & TPS_GRAPH) ? reduced_solve_graph(P, lv, H->streams[0])
                                     : reduced_solve(P, lv, H->streams[0]);
@@ -592,9 +597,20 @@ tps_status tps_solve_host_many_async(tps_plan_t P, int64_t count, int64_t n,
   if (e == cudaSuccess) e = cudaEventRecord(P->lane_ev[0], us);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(P->lane[i], P->lane_ev[0], 0);
   if (e != cudaSuccess) return TPS_ERR_CUDA;
+  // the uploads of consecutive systems follow one another (system k starts
+  // once system k-1's rows are all on the device), so at any time one
+  // system uploads while the one before it finishes and downloads, instead
+  // of both buffer sets uploading at once and then downloading at once
   tps_status st = TPS_OK;
   for (int64_t k = 0; k < count && st == TPS_OK; ++k) {
     tps_plan_s* Q = (k & 1) ? T : P;
+    if (k > 0) {
+      tps_plan_s* prev = (k & 1) ? P : T;
+      if (cudaStreamWaitEvent(P->lane[k & 1], prev->pipe->ev_up, 0) != cudaSuccess) {
+        st = TPS_ERR_CUDA;
+        break;
+      }
+    }
     st = tps_solve_host_async(Q, n, a[k], b[k], c[k], d[k], x[k], P->lane[k & 1]);
   }
   // join both buffer sets back into the caller's stream, also after an error
