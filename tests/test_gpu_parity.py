@@ -308,6 +308,35 @@ def test_host_many_overlaps_systems_and_matches_oracle(dtype, S, flags):
         assert oracle.rel_forward_error(x.numpy().astype(np.float64), ref) <= tol
 
 
+@pytest.mark.parametrize("n,chunk", [(1, 0), (64, 0), (65, 0), (1000, 100), (70001, 4096)])
+def test_host_many_small_and_ragged_sizes(n, chunk):
+    systems, refs, tdt = host_systems("f64_df", n, [800 + k for k in range(4)])
+    xs = [torch.full((n,), float("nan"), dtype=tdt).pin_memory() for _ in range(4)]
+    plan = binding.Plan(n, dtype="f64_df", residency="host", streams=4, chunk=chunk,
+                        flags=binding.HOST_OVERLAP)
+    plan.solve_host_many(systems, xs)
+    torch.cuda.synchronize()
+    assert plan.query()["status"] == 0
+    for x, ref in zip(xs, refs):
+        assert oracle.rel_forward_error(x.numpy(), ref) <= F64_FWD
+
+
+def test_host_many_zero_copy_from_pageable_memory():
+    n = 200003
+    plan = binding.Plan(n, dtype="f64", residency="host", streams=2,
+                        flags=binding.HOST_OVERLAP | binding.ZERO_COPY)
+    if not plan.query()["pageable_ok"]:
+        pytest.skip("the device does not access pageable host memory coherently")
+    systems, refs, _ = host_systems("f64", n, [900, 901, 902])
+    systems = [tuple(t.clone() for t in sy) for sy in systems]  # pageable copies
+    xs = [torch.full((n,), float("nan"), dtype=torch.float64) for _ in range(3)]
+    plan.solve_host_many(systems, xs)
+    torch.cuda.synchronize()
+    assert plan.query()["status"] == 0
+    for x, ref in zip(xs, refs):
+        assert oracle.rel_forward_error(x.numpy(), ref) <= F64_FWD
+
+
 def test_host_many_reports_the_twins_systems_and_checks_outputs():
     n = 100003
     systems, refs, tdt = host_systems("f64_df", n, [71, 72, 71])
