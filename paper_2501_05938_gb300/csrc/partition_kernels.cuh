@@ -247,6 +247,25 @@ __device__ __forceinline__ int warp_chunks(const Level& lv, int64_t k0, int nb, 
 __device__ __forceinline__ int warp_lmin(const Level& lv, int64_t k0, int nb) {
   return (k0 + nb == lv.p) ? min(lv.m, lv.llast) : lv.m;
 }
+// the block length every active lane of the warp has, or 0 if they differ
+__device__ __forceinline__ int warp_luni(const Level& lv, int64_t k0, int nb) {
+  return (k0 + nb == lv.p) ? (lv.llast == lv.m ? lv.m : 0) : lv.m;
+}
+
+// Chunks that every active lane sees the same way run unrolled: all rows
+// interior (kMid), the block's first row f and then interior rows (kFirst,
+// chunk 0), or interior rows and then the block's last row l (kLast, when
+// every lane's block ends with the chunk).  Any other chunk (a ragged last
+// block, a packed-system boundary in or next to the chunk) goes row by row.
+enum ChunkKind : int { kSlow = -1, kMid = 0, kFirst = 1, kLast = 2 };
+__device__ __forceinline__ int chunk_kind(int ch, int row0, int R, int lmin, int luni,
+                                          bool clean) {
+  if (!clean) return kSlow;
+  if (ch >= 1 && row0 + R <= lmin - 1) return kMid;
+  if (ch == 0 && R <= lmin - 1) return kFirst;
+  if (ch >= 1 && luni > 0 && row0 + R == luni) return kLast;
+  return kSlow;
+}
 
 // ------------------------------------------------------------------ Stage 1
 // R rows per chunk; a checkpoint every K rows (K the chunk length of
@@ -272,6 +291,7 @@ __global__ void __launch_bounds__(W * 32)
   const int L = active ? block_len(lv, k) : 0;
   const int nch = warp_chunks(lv, k0, nb, R);
   const int lmin = warp_lmin(lv, k0, nb);
+  const int luni = warp_luni(lv, k0, nb);
 
   Tin* tile = reinterpret_cast<Tin*>(smem_raw) + warp * 2 * TL::kBuf;
   const Tin* const srcs[4] = {a, b, c, d};
@@ -333,18 +353,34 @@ __global__ void __launch_bounds__(W * 32)
     cp_async_wait<1>();
     __syncwarp();
     const Tin* t = tile + (ch & 1) * TL::kBuf + lane * TL::kStride;
-    const bool fast = ch >= 1 && row0 + R <= lmin - 1 &&
-                      !__any_sync(0xffffffffu, bd.cnt > 0 && bd.touches(start + row0, R));
-    if (fast) {
+    const bool clean = !__any_sync(0xffffffffu, bd.cnt > 0 && bd.touches(start + row0, R));
+    const int kind = chunk_kind(ch, row0, R, lmin, luni, clean);
+    if (kind != kSlow) {
+      // one unrolled body for the three kinds: only row 0 and row R-1 test
+      // (warp-uniformly) whether they are the block's f or l row
+      const bool first = kind == kFirst, last = kind == kLast;
 #pragma unroll
       for (int r = 0; r < R; r += V) {
         const Vec16<Tin> xa = lds16(t + r), xb = lds16(t + TL::kArr + r),
                          xc = lds16(t + 2 * TL::kArr + r), xd = lds16(t + 3 * TL::kArr + r);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-          interior(Ar::from(xa.v[v]), Ar::from_pivot(xb.v[v]), Ar::from(xc.v[v]), Ar::from(xd.v[v]));
-          if constexpr (R > K) {  // chunk spans several checkpoint intervals
-            if ((r + v + 1) % K == 0 && r + v + 1 < R) checkpoint(row0 + r + v);
+          const int rr = r + v;
+          const T av = Ar::from(xa.v[v]), bv = Ar::from_pivot(xb.v[v]), cv = Ar::from(xc.v[v]),
+                  dv = Ar::from(xd.v[v]);
+          if (rr == 0 && first) {  // the block's first row: f's equation
+            a0 = av; b0 = bv; c0 = cv; d0 = dv;
+          } else if (rr == R - 1 && last) {  // the block's last row
+            const T ratio = Ar::mul_nn(av, rbp);
+            beta = Ar::sub_mul_dom(bv, ratio, cprev);
+            g = Ar::sub_mul(dv, ratio, g);
+            al = Ar::mul_neg_nn(ratio, al);
+            clast = cv;
+          } else {
+            interior(av, bv, cv, dv);
+            if constexpr (R > K) {  // chunk spans several checkpoint intervals
+              if ((rr + 1) % K == 0 && rr + 1 < R) checkpoint(row0 + rr);
+            }
           }
         }
       }
@@ -437,6 +473,7 @@ __global__ void __launch_bounds__(W * 32)
   const int L = active ? block_len(lv, k) : 0;
   const int nch = warp_chunks(lv, k0, nb, R);
   const int lmin = warp_lmin(lv, k0, nb);
+  const int luni = warp_luni(lv, k0, nb);
 
   unsigned char* wbase = smem_raw + warp * TL3::kBytesPerWarp;
   Tin* tile = reinterpret_cast<Tin*>(wbase);
@@ -489,9 +526,13 @@ __global__ void __launch_bounds__(W * 32)
       gp = Ar::from(ck[lane]);
       zp = Ar::sub_mul(Ar::from(ck[32 + lane]), Ar::from(ck[64 + lane]), f);
     }
-    const bool fast = ch >= 1 && row0 + R <= lmin - 1 &&
-                      !__any_sync(0xffffffffu, bd.cnt > 0 && bd.touches(start + row0, R));
-    if (fast) {
+    const bool clean = !__any_sync(0xffffffffu, bd.cnt > 0 && bd.touches(start + row0, R));
+    const int kind = chunk_kind(ch, row0, R, lmin, luni, clean);
+    if (kind != kSlow) {
+      // unrolled chunk: forward over the interior rows, back-substitution
+      // from the row below; only row 0 (kFirst: f) and row R-1 (kLast: l)
+      // test their role, warp-uniformly
+      const bool first = kind == kFirst, last = kind == kLast;
       T Z[R], G[R];
       Tin xo[R];
 #pragma unroll
@@ -500,20 +541,28 @@ __global__ void __launch_bounds__(W * 32)
                          xc = lds16(t + 2 * TL::kArr + r), xd = lds16(t + 3 * TL::kArr + r);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
+          const int rr = r + v;
+          if ((rr == 0 && first) || (rr == R - 1 && last)) continue;
           const T av = Ar::from(xa.v[v]);
           const T beta = Ar::sub_mul_dom(Ar::from(xb.v[v]), av, gp);
           bad |= Ar::bad_pivot(beta);
           const T rbeta = Ar::rcp(beta);
           zp = Ar::mul_nn(Ar::sub_mul(Ar::from(xd.v[v]), av, zp), rbeta);
           gp = Ar::mul_nn(Ar::from(xc.v[v]), rbeta);
-          Z[r + v] = zp;
-          G[r + v] = gp;
+          Z[rr] = zp;
+          G[rr] = gp;
         }
       }
 #pragma unroll
       for (int r = R - 1; r >= 0; --r) {
-        xnext = Ar::sub_mul(Z[r], G[r], xnext);
-        Ar::to(xo[r], xnext);
+        if (r == R - 1 && last) {
+          Ar::to(xo[r], l);  // xnext is l already
+        } else if (r == 0 && first) {
+          Ar::to(xo[r], f);
+        } else {
+          xnext = Ar::sub_mul(Z[r], G[r], xnext);
+          Ar::to(xo[r], xnext);
+        }
       }
 #pragma unroll
       for (int r = 0; r < R; r += V) {
