@@ -602,7 +602,8 @@ def main():
     dom_ms = max(s1, s3)
     alg_bytes = (32 if dominant == "k_stage1" else 40) * n
     achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
-    traffic = traffic_table().get(f"{dominant}_f64_df")
+    tt = traffic_table()
+    traffic = tt.get(f"{dominant}_f64_df_m{info['m']}", tt.get(f"{dominant}_f64_df"))
     kernel_hash = kernel_source_hash()
     levels = info["levels"]
     launches_per_step = 2 * levels + 1
