@@ -123,7 +123,7 @@ class Plan:
         return self._h
 
     def close(self):
-        if self._h:
+        if getattr(self, "_h", None):
             lib().tps_plan_destroy(self._h)
             self._h = ctypes.c_void_p()
 

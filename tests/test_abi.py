@@ -1,6 +1,8 @@
 """The C ABI without a GPU: the library loads, exports every function
 include/tps.h declares, and rejects bad plan descriptors on the host."""
 import ctypes
+
+import numpy as np
 import os
 import re
 
@@ -98,3 +100,23 @@ def test_null_arguments(lib):
     assert lib.tps_plan_query(None, None) == 1
     sz = ctypes.c_size_t()
     assert lib.tps_workspace_size(None, ctypes.byref(sz)) == 1
+
+
+def test_binding_checks_tensor_type_layout_and_length():
+    # argument marshalling only: no plan, no library call is needed to reject these
+    torch = pytest.importorskip("torch")
+    plan = binding.Plan.__new__(binding.Plan)  # the checks use only the plan's dtype
+    plan.dtype = "f64_df"
+    good = [torch.zeros(10, dtype=torch.float64) for _ in range(5)]
+    plan._arrays(10, *good)
+    for bad in (torch.zeros(10, dtype=torch.float32), torch.zeros(20, dtype=torch.float64)[::2],
+                torch.zeros(11, dtype=torch.float64)):
+        with pytest.raises(binding.TpsError):
+            plan._arrays(10, *good[:4], bad)
+    plan.dtype = "f32"
+    with pytest.raises(binding.TpsError):
+        plan._arrays(10, *good)
+    with pytest.raises(binding.TpsError):  # offsets the kernels read are int64
+        binding.Plan._offsets(torch.zeros(3, dtype=torch.int32), None)
+    keep, ptr = binding.Plan._offsets(torch.zeros(3, dtype=torch.int64), [0, 5, 10])
+    assert keep.dtype == np.int64 and ptr.value == keep.ctypes.data
