@@ -1,11 +1,10 @@
 """The C ABI without a GPU: the library loads, exports every function
 include/tps.h declares, and rejects bad plan descriptors on the host."""
 import ctypes
-
-import numpy as np
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2501_05938_gb300 import binding
