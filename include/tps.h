@@ -251,7 +251,10 @@ tps_status tps_solve_host_async(tps_plan_t plan, int64_t n, const void* a, const
  *               or any input of systems k-1, k, k+1 (TPS_ERR_INVALID_ARG)
  * Stream-ordered on `stream` as one operation (it starts after the work
  * already in `stream`, and `stream` waits for every system); returns after
- * enqueueing.  Numeric status of all systems: tps_plan_query on the plan. */
+ * enqueueing.  If the arrays of system k are rejected (the checks of
+ * tps_solve_host_async), systems 0 .. k-1 stay enqueued and `stream` still
+ * waits for them.  Numeric status of all systems: tps_plan_query on the
+ * plan. */
 tps_status tps_solve_host_many_async(tps_plan_t plan, int64_t count, int64_t n,
                                      const void* const* a, const void* const* b,
                                      const void* const* c, const void* const* d,
