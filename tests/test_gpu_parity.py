@@ -361,6 +361,15 @@ def test_host_many_reports_the_twins_systems_and_checks_outputs():
         plan.solve_host_many(systems[:2], [x0, x0])
     with pytest.raises(binding.TpsError):  # an output overlaps the next system's input
         plan.solve_host_many(systems[:2], [systems[1][3], x1])
+    # system 1's arrays are rejected: system 0 stays enqueued and completes
+    x0.fill_(float("nan"))
+    dev_b = systems[1][1].cuda()
+    with pytest.raises(binding.TpsError):
+        plan.solve_host_many([systems[0], (systems[1][0], dev_b, systems[1][2], systems[1][3])],
+                             [x0, x1])
+    torch.cuda.synchronize()
+    assert plan.query()["status"] == 0
+    assert oracle.rel_forward_error(x0.numpy(), refs[0]) <= F64_FWD
     plain = binding.Plan(n, dtype="f64_df", residency="host", streams=2)
     with pytest.raises(binding.TpsError):  # the plan has no twin
         plain.solve_host_many(systems[:2], [x0, x1])
