@@ -75,6 +75,29 @@ def test_fp64_paths_match_oracle(dtype, n, m, onchip):
         assert fwd <= 1e-14 and res <= 1e-15, (fwd, res)
 
 
+@pytest.mark.parametrize("m", [16, 24, 64])
+@pytest.mark.parametrize("tail", [0, 1, 5, 9])
+@pytest.mark.parametrize("dtype", ["f64_df", "f32"])
+def test_chunk_kinds_at_block_and_warp_edges(m, tail, dtype):
+    """Block counts that end a warp exactly, one block into a warp, or one
+    short of it, with a last block of m, m + 1 (merged one-row tail), or a
+    few rows: the unrolled first/last-chunk paths and the row-by-row path
+    meet at these edges."""
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    fwd_tol, res_tol = (F32_FWD, F32_RES) if dtype == "f32" else (F64_FWD, F64_RES)
+    for p in (32 * 40, 32 * 40 + 1, 32 * 41 - 1):
+        n = p * m + tail
+        s = synth.system(3000 + n, n)
+        if dtype == "f32":
+            s = synth.to_f32(s)
+        x, info = run(binding.Plan(n, dtype=dtype, m=m, flags=binding.NO_ONCHIP), s, tdt)
+        assert info["status"] == 0
+        a, b, c, d = (np.asarray(s[k], dtype=np.float64) for k in "abcd")
+        ref = oracle.thomas(a, b, c, d)
+        assert oracle.rel_forward_error(x, ref) <= fwd_tol, (p, n)
+        assert oracle.rel_residual(a, b, c, d, x) <= res_tol, (p, n)
+
+
 @pytest.mark.parametrize("n,m,mr", [(1 << 16, 256, 4), (1 << 18, 2, 8), (50000, 1000, 1000)])
 def test_reduced_block_sizes(n, m, mr):
     """Unusual block sizes on the level-by-level route (the on-chip solve
