@@ -61,8 +61,8 @@ static cudaEvent_t* next_trace(tps_plan_s* P) {
 }
 
 // Defaults when the caller leaves a parameter at 0 and no predictor is asked
-// for.  Block size 128: at n = 2^27 within 1.1% of the best block size on
-// every GB300 measured (m = 256 is 1.1% faster on some boxes and 2.4% slower
+// for.  Block size 128: at n = 2^27 within 1.4% of the best block size on
+// every GB300 measured (m = 64 is 1.4% faster on some boxes and 2.1% slower
 // on others; tps_autotune picks per box); a small system keeps at least ~4
 // blocks per SM so the per-lane serial sweeps run in parallel.
 static void default_params(const tps_plan_desc& d, int32_t& m, int32_t& mr, int32_t& S) {
