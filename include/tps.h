@@ -26,8 +26,9 @@
  *   through tps_plan_query, not by the return value.
  *   Calls are stream-ordered and asynchronous: argument and launch errors
  *   come back as the return value, numeric errors (TPS_ERR_ZERO_PIVOT,
- *   TPS_ERR_NO_CONVERGENCE) from tps_plan_query after the stream has been
- *   synchronised.  A plan may be used by one stream at a time.
+ *   TPS_ERR_RANGE, TPS_ERR_NO_CONVERGENCE) from tps_plan_query after the
+ *   stream has been synchronised.  A plan may be used by one stream at a
+ *   time.
  *   A plan belongs to the device that is current when tps_plan creates it:
  *   every later call on it needs that device current, and its device
  *   arrays on that device (or managed), else TPS_ERR_INVALID_ARG.  Distinct
@@ -53,7 +54,9 @@ typedef enum {
   TPS_ERR_OOM = 4,            /* device or pinned allocation failed            */
   TPS_ERR_ZERO_PIVOT = 5,     /* zero/non-finite pivot met (matrix not SDD)    */
   TPS_ERR_NO_CONVERGENCE = 6, /* mixed-precision refinement did not converge   */
-  TPS_ERR_TIMEOUT = 7         /* a bounded device-side wait gave up            */
+  TPS_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up            */
+  TPS_ERR_RANGE = 8           /* an input or x outside what the arithmetic     */
+                              /* represents (see TPS_F64_DF)                   */
 } tps_status;
 
 typedef enum {
@@ -62,10 +65,22 @@ typedef enum {
   TPS_MIXED_F32_F64 = 2, /* fp64 I/O; fp32 elimination, fp64 residual/update,   */
                          /* iterative refinement to the plan's tolerance        */
   TPS_F64_DF = 3         /* fp64 I/O; double-float arithmetic (pairs of fp32)   */
-                         /* on the fp32 pipes, about 2^-46 relative per op;     */
-                         /* for magnitudes in [2^-103, 2^127]; a diagonal entry */
-                         /* beyond that range, infinite or NaN is reported as   */
-                         /* a pivot failure, in a, c, d it is not detected      */
+                         /* on the fp32 pipes, about 2^-46 relative per op.     */
+                         /* Each row is scaled exactly by the power of two that */
+                         /* brings b[i] into [1, 2), so any fp64 scaling of the */
+                         /* rows is served (x unchanged).  The pairs hold x at  */
+                         /* full precision while max |d[i] / b[i]| lies in      */
+                         /* [2^-84, 2^84].  Reported after the solve            */
+                         /* (tps_plan_query): TPS_ERR_ZERO_PIVOT for a b[i]     */
+                         /* that is 0, subnormal, infinite or NaN;              */
+                         /* TPS_ERR_RANGE for an a[i], c[i] or d[i] above        */
+                         /* 2^84 |b[i]| (or not finite), for a system whose     */
+                         /* |d[i] / b[i]| is below 2^-84 in every row with      */
+                         /* d[i] != 0, for an entry taken as 0 (a[i], c[i]      */
+                         /* below 2^-103 |b[i]|, d[i] below 2^-129 |b[i]|) in a */
+                         /* row whose |b[i]| is so large against the system    */
+                         /* that the residual could suffer, and for an x at or  */
+                         /* above 2^101.  TPS_F64 has none of these limits.     */
 } tps_dtype;
 
 typedef enum {
@@ -279,8 +294,8 @@ tps_status tps_solve_host_many_async(tps_plan_t plan, int64_t count, int64_t n,
  *               current device; only alignment and overlap are checked (no
  *               pointer queries on this path)
  *   status_out  optional device int32 that receives TPS_OK,
- *               TPS_ERR_ZERO_PIVOT or TPS_ERR_TIMEOUT when the solve has run
- *               (NULL: not reported)
+ *               TPS_ERR_ZERO_PIVOT, TPS_ERR_TIMEOUT or TPS_ERR_RANGE when
+ *               the solve has run (NULL: not reported)
  *   stream      cudaStream_t as void*
  * A system that fits in shared memory (every accepted size on a 152-SM
  * GB300) is solved by the single-launch on-chip solve (see tps_solve);
@@ -382,7 +397,10 @@ int32_t tps_paper_predict_streams(double size, const double* sum_model, const do
 
 /* Report the plan's parameters and the numeric status of the solves since
  * the previous query (synchronises the plan's last stream, reads the device
- * status word and clears it). */
+ * status word and clears it).  Several conditions at once report the first
+ * of TPS_ERR_ZERO_PIVOT, TPS_ERR_TIMEOUT, TPS_ERR_RANGE,
+ * TPS_ERR_NO_CONVERGENCE.  Every dtype reports TPS_ERR_RANGE for an x that
+ * is not finite. */
 tps_status tps_plan_query(tps_plan_t plan, tps_info* out);
 
 /* Static description of a status code. */

@@ -15,7 +15,7 @@ LIB_PATH = os.environ.get("TPS_LIB_PATH") or os.path.join(HERE, "libtps.so")
 TPS_OK = 0
 STATUS = {0: "TPS_OK", 1: "TPS_ERR_INVALID_ARG", 2: "TPS_ERR_UNSUPPORTED", 3: "TPS_ERR_CUDA",
           4: "TPS_ERR_OOM", 5: "TPS_ERR_ZERO_PIVOT", 6: "TPS_ERR_NO_CONVERGENCE",
-          7: "TPS_ERR_TIMEOUT"}
+          7: "TPS_ERR_TIMEOUT", 8: "TPS_ERR_RANGE"}
 DTYPES = {"f64": 0, "f32": 1, "mixed": 2, "f64_df": 3}
 RESIDENCY = {"device": 0, "host": 1}
 TUNE_PREDICT, TUNE_EXHAUSTIVE, TRACE, EXTERNAL_WORKSPACE, GRAPH, ZERO_COPY, NO_ONCHIP = (

@@ -14,6 +14,7 @@
 // must be serialised by the caller.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <mutex>
 
 #include "tps_internal.h"
@@ -98,16 +99,22 @@ bool aligned16(int m, const void* const* p, int k) {
   return true;
 }
 
+// dmax: the system's range codes at level 0 of a double-float solve (zero
+// before the call, zero again after it), else null.
 template <class Ar, class Tin, class Tred>
 cudaError_t run(unsigned char* ws, const Layout& L, int idx, int64_t n, const Tin* a,
-                const Tin* b, const Tin* c, const Tin* d, Tin* x, int* st, cudaStream_t s) {
+                const Tin* b, const Tin* c, const Tin* d, Tin* x, int* st, cudaStream_t s,
+                unsigned* dmax) {
   if (idx == L.levels) {
-    k_base<Ar, Tin, Tin><<<1, 32, 0, s>>>(n, a, b, c, d, x, nullptr, 0, st);
+    k_base<Ar, Tin, Tin><<<1, 32, 0, s>>>(n, a, b, c, d, x, nullptr, 0, st, dmax);
+    if (dmax) k_dcode_check<<<1, 256, 0, s>>>(dmax, 1, st);
     return cudaGetLastError();
   }
   const LevelPlan& P = L.lv[idx];
-  constexpr int K = sizeof(Tin) >= 8 ? 8 : 16;  // Stage-3 chunk rows, checkpoint spacing
+  constexpr int K = kChunkRows<Tin>;  // Stage-3 chunk rows, checkpoint spacing (as make_layout)
   constexpr int R1 = K;
+  Level lv = P.lv;
+  lv.dmax = dmax;
   Tred* red[5];
   for (int i = 0; i < 5; ++i) red[i] = reinterpret_cast<Tred*>(ws + P.off_red[i]);
   Tred* ck[3];
@@ -117,14 +124,15 @@ cudaError_t run(unsigned char* ws, const Layout& L, int idx, int64_t n, const Ti
   const void* in5[5] = {a, b, c, d, x};
   if (aligned16<Tin>(P.lv.m, in4, 4))
     k_stage1<Ar, Tin, Tred, R1, K, 1, true><<<grid, 32, Tile<Tin, R1>::kBytesPerWarp, s>>>(
-        P.lv, a, b, c, d, red[0], red[1], red[2], red[3], ck[0], ck[1], ck[2], st);
+        lv, a, b, c, d, red[0], red[1], red[2], red[3], ck[0], ck[1], ck[2], st);
   else
     k_stage1<Ar, Tin, Tred, R1, K, 1, false><<<grid, 32, Tile<Tin, R1>::kBytesPerWarp, s>>>(
-        P.lv, a, b, c, d, red[0], red[1], red[2], red[3], ck[0], ck[1], ck[2], st);
+        lv, a, b, c, d, red[0], red[1], red[2], red[3], ck[0], ck[1], ck[2], st);
+  if (dmax) k_dcode_check<<<1, 256, 0, s>>>(dmax, 1, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = run<Ar, Tred, Tred>(ws, L, idx + 1, 2 * P.lv.p, red[0], red[1], red[2], red[3], red[4],
-                          st, s);
+                          st, s, nullptr);
   if (e != cudaSuccess) return e;
   if (aligned16<Tin>(P.lv.m, in5, 5))
     k_stage3<Ar, Tin, Tred, K, 1, true><<<grid, 32, Tile3<Tin, Tred, K>::kBytesPerWarp, s>>>(
@@ -138,7 +146,18 @@ cudaError_t run(unsigned char* ws, const Layout& L, int idx, int64_t n, const Ti
 // Translate the status bits into a tps_status for the caller's output.
 __global__ void k_report(const int* st, int32_t* out) {
   const int w = *st;
-  *out = (w & ST_BAD_PIVOT) ? TPS_ERR_ZERO_PIVOT : (w & ST_TIMEOUT) ? TPS_ERR_TIMEOUT : TPS_OK;
+  *out = (w & ST_BAD_PIVOT) ? TPS_ERR_ZERO_PIVOT
+         : (w & ST_TIMEOUT) ? TPS_ERR_TIMEOUT
+         : (w & ST_RANGE)   ? TPS_ERR_RANGE
+                            : TPS_OK;
+}
+
+// A cooperative launch the device refuses for its size or resources (fewer
+// SMs than the cached occupancy assumed, e.g. under an SM partition):
+// the level-by-level route serves instead.
+bool launch_refused(cudaError_t e) {
+  return e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorLaunchOutOfResources ||
+         e == cudaErrorInvalidConfiguration;
 }
 
 bool overlap(const void* p, const void* q, size_t bytes) {
@@ -167,28 +186,41 @@ extern "C" tps_status tps_solve_noalloc(int32_t dtype, int64_t n, const void* a,
   if (ts != TPS_OK) return ts;
   cudaStream_t s = (cudaStream_t)stream;
   int* st = reinterpret_cast<int*>(ws);
-  // the status word is the only scratch that must start from zero; the
+  // the first 64 bytes (status word, on-chip barrier counter, the three
+  // range codes at 40) are the only scratch that must start from zero; the
   // reduced systems and checkpoints are fully rewritten by every call
-  cudaError_t e = cudaMemsetAsync(st, 0, sizeof(int), s);
+  unsigned* dmax = dtype == TPS_F64_DF ? reinterpret_cast<unsigned*>(ws + 40) : nullptr;
+  cudaError_t e = cudaMemsetAsync(st, 0, 64, s);
   // the whole system in one on-chip launch where it fits (its barrier
-  // counter and exchange rows sit where the levels would go)
+  // counter and exchange rows sit where the levels would go); a test switch
+  // (TPS_TEST_NOALLOC_LEVELS=1) keeps the level-by-level route
   bool onchip = false;
-  if (e == cudaSuccess)
-    e = onchip_solve(dtype, n, a, b, c, d, x, ws + align_up(64), reinterpret_cast<unsigned*>(ws + 32),
-                     st, s, onchip);
+  const char* lvl = std::getenv("TPS_TEST_NOALLOC_LEVELS");
+  if (e == cudaSuccess && !(lvl && lvl[0] == '1')) {
+    e = onchip_solve(dtype, n, a, b, c, d, x, ws + align_up(64),
+                     reinterpret_cast<unsigned*>(ws + 32), st, s, onchip, dmax);
+    if (e != cudaSuccess && launch_refused(e)) {
+      cudaGetLastError();
+      e = cudaSuccess;
+      onchip = false;
+    }
+  }
   if (e == cudaSuccess && !onchip) {
     switch (dtype) {
       case TPS_F64:
         e = run<ArF64, double, double>(ws, L, 0, n, (const double*)a, (const double*)b,
-                                       (const double*)c, (const double*)d, (double*)x, st, s);
+                                       (const double*)c, (const double*)d, (double*)x, st, s,
+                                       nullptr);
         break;
       case TPS_F64_DF:
         e = run<ArDF, double, float2>(ws, L, 0, n, (const double*)a, (const double*)b,
-                                      (const double*)c, (const double*)d, (double*)x, st, s);
+                                      (const double*)c, (const double*)d, (double*)x, st, s,
+                                      dmax);
         break;
       default:
         e = run<ArF32, float, float>(ws, L, 0, n, (const float*)a, (const float*)b,
-                                     (const float*)c, (const float*)d, (float*)x, st, s);
+                                     (const float*)c, (const float*)d, (float*)x, st, s,
+                                     nullptr);
         break;
     }
   }

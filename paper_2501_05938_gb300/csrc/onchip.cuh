@@ -71,8 +71,10 @@ struct AccL0 {
   using T = typename Ar::T;
   Tin* p[4];
   int r0;
-  __device__ __forceinline__ T ld(int k, int r) const {
-    return k == 1 ? Ar::from_pivot(p[1][r0 + r]) : Ar::from(p[k][r0 + r]);  // b: checked
+  // row r, scaled and range-checked like the multi-launch path's rows
+  __device__ __forceinline__ void row(int r, T& av, T& bv, T& cv, T& dv, RowChk& k) const {
+    Ar::template row<true>(p[0][r0 + r], p[1][r0 + r], p[2][r0 + r], p[3][r0 + r], av, bv, cv,
+                           dv, k);
   }
   __device__ __forceinline__ T rel(int k, int r) const {
     return *reinterpret_cast<const T*>(&p[k][r0 + r]);
@@ -89,7 +91,10 @@ struct AccLv {
   using T = typename Ar::T;
   T* p[4];
   int r0;
-  __device__ __forceinline__ T ld(int k, int r) const { return p[k][lvx(r0 + r)]; }
+  __device__ __forceinline__ void row(int r, T& av, T& bv, T& cv, T& dv, RowChk&) const {
+    const int i = lvx(r0 + r);
+    av = p[0][i]; bv = p[1][i]; cv = p[2][i]; dv = p[3][i];
+  }
   __device__ __forceinline__ T rel(int k, int r) const { return p[k][lvx(r0 + r)]; }
   __device__ __forceinline__ void set_rel(int k, int r, T v) const { p[k][lvx(r0 + r)] = v; }
   __device__ __forceinline__ void set_x(int r, T v) const { p[3][lvx(r0 + r)] = v; }
@@ -101,14 +106,17 @@ struct AccLv {
 // alpha/beta) written over its a, b, c.  red: the first reduced row
 // (l_prev, f, l) and the last (f, l, f_next), four coefficients each.
 template <class Ar, class Acc>
-__device__ __forceinline__ void oc_fwd(const Acc& A, int L, typename Ar::T* red, bool& bad) {
+__device__ __forceinline__ void oc_fwd(const Acc& A, int L, typename Ar::T* red, bool& bad,
+                                       RowChk& chk) {
   using T = typename Ar::T;
-  const T a0 = A.ld(0, 0), b0 = A.ld(1, 0), c0 = A.ld(2, 0), d0 = A.ld(3, 0);
+  T a0, b0, c0, d0;
+  A.row(0, a0, b0, c0, d0, chk);
   T rbp = Ar::one(), cprev = Ar::zero(), g = Ar::zero(), al = Ar::neg(Ar::one());
   T P = Ar::zero(), Q = Ar::zero(), S = Ar::neg(Ar::one());
 #pragma unroll 1
   for (int j = 1; j < L - 1; ++j) {
-    const T av = A.ld(0, j), bv = A.ld(1, j), cv = A.ld(2, j), dv = A.ld(3, j);
+    T av, bv, cv, dv;
+    A.row(j, av, bv, cv, dv, chk);
     const T ratio = Ar::mul(av, rbp);
     const T beta = Ar::sub_mul_dom(bv, ratio, cprev);
     g = Ar::sub_mul(dv, ratio, g);
@@ -125,7 +133,8 @@ __device__ __forceinline__ void oc_fwd(const Acc& A, int L, typename Ar::T* red,
     rbp = rbeta;
     cprev = cv;
   }
-  const T av = A.ld(0, L - 1), bv = A.ld(1, L - 1), cv = A.ld(2, L - 1), dv = A.ld(3, L - 1);
+  T av, bv, cv, dv;
+  A.row(L - 1, av, bv, cv, dv, chk);
   const T ratio = Ar::mul(av, rbp);
   const T beta = Ar::sub_mul_dom(bv, ratio, cprev);
   g = Ar::sub_mul(dv, ratio, g);
@@ -171,6 +180,7 @@ __device__ __forceinline__ void oc_reduce_levels(typename Ar::T* const* lv, int 
                                                  OcLevels& L, bool& bad) {
   using T = typename Ar::T;
   T red[8];
+  RowChk nochk;  // the level rows are computed pairs, not inputs
   L.off = 0;
   L.N = N1;
   L.nl = 0;
@@ -180,7 +190,7 @@ __device__ __forceinline__ void oc_reduce_levels(typename Ar::T* const* lv, int 
     if (tid < pl) {
       const int len = tid == pl - 1 ? L.N - kOcBlock * (pl - 1) : kOcBlock;
       const AccLv<Ar> A{{lv[0], lv[1], lv[2], lv[3]}, L.off + kOcBlock * tid};
-      oc_fwd<Ar>(A, len, red, bad);
+      oc_fwd<Ar>(A, len, red, bad, nochk);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         lv[q][lvx(noff + 2 * tid)] = red[q];
@@ -246,7 +256,7 @@ __global__ void __launch_bounds__(kOcThreads, 1)
     k_onchip(int64_t n, int mt, int64_t p, const Tin* __restrict__ a, const Tin* __restrict__ b,
              const Tin* __restrict__ c, const Tin* __restrict__ d, Tin* __restrict__ x,
              typename Ar::T* __restrict__ xch, unsigned* __restrict__ bar, unsigned arrivals,
-             int* __restrict__ status, int vec16) {
+             int* __restrict__ status, int vec16, unsigned* __restrict__ dmax) {
   using T = typename Ar::T;
   using Lay = OcLayout<Ar, Tin>;
   static_assert(sizeof(T) <= sizeof(Tin), "relations are stored in the input slots");
@@ -288,11 +298,12 @@ __global__ void __launch_bounds__(kOcThreads, 1)
   bool bad = false;
   T red[8];
   int L0len = 0;
+  RowChk chk;
   if (tid < nb) {
     const int64_t k = kb + tid;
     L0len = k == p - 1 ? (int)(n - k * mt) : mt;
     const AccL0<Ar, Tin> A{{s0[0], s0[1], s0[2], s0[3]}, (int)(k * mt - r0)};
-    oc_fwd<Ar>(A, L0len, red, bad);
+    oc_fwd<Ar>(A, L0len, red, bad, chk);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       lv[q][lvx(2 * tid)] = red[q];
@@ -300,6 +311,12 @@ __global__ void __launch_bounds__(kOcThreads, 1)
     }
   }
   __syncthreads();
+
+  // the rows' range: the system's range codes (one set of atomics per
+  // warp), a, c, d too large or b invalid
+  if (dmax) codes_raise_warp(dmax, 0, true, chk);
+  if (chk.range_bad()) atomicOr(status, ST_RANGE);
+  bad |= chk.b_bad();
 
   // ---- Stage 1, levels 1..: 8-row blocks until one block is left
   OcLevels lev;
@@ -309,7 +326,8 @@ __global__ void __launch_bounds__(kOcThreads, 1)
   const int M = 2 * G;
   if (tid == 0) {
     const AccLv<Ar> A{{lv[0], lv[1], lv[2], lv[3]}, off};
-    oc_fwd<Ar>(A, N, red, bad);
+    RowChk nochk;
+    oc_fwd<Ar>(A, N, red, bad, nochk);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       xch[q * M + 2 * cta] = red[q];
@@ -339,6 +357,12 @@ __global__ void __launch_bounds__(kOcThreads, 1)
   }
   __syncthreads();
   if (!ok_s) return;
+  // every CTA's codes are in: judge the system's range
+  if (dmax && cta == 0 && tid == 0) {
+    if (range_codes_bad(ld_l2(dmax), ld_l2(dmax + 1), ld_l2(dmax + 2)))
+      atomicOr(status, ST_RANGE);
+    dmax[0] = dmax[1] = dmax[2] = 0u;  // zero again for the next solve
+  }
 
   // ---- Stage 2: the 2G interface rows by parallel cyclic reduction
   for (int i = tid; i < M; i += kOcThreads) {
@@ -404,6 +428,9 @@ __global__ void __launch_bounds__(kOcThreads, 1)
   for (int i = tid; i < nv; i += kOcThreads)
     *reinterpret_cast<float4*>(x + r0 + i * V) = *reinterpret_cast<const float4*>(s0[3] + i * V);
   for (int i = nv * V + tid; i < rows; i += kOcThreads) x[r0 + i] = s0[3][i];
+  bool oob = false;
+  for (int i = tid; i < rows; i += kOcThreads) oob |= Ar::out_bad(s0[3][i]);
+  if (oob) atomicOr(status, ST_RANGE);
 }
 
 }  // namespace tps
@@ -448,7 +475,8 @@ template <class Ar, class Tin>
 __global__ void __launch_bounds__(kWinThreads)
     k_window(int64_t n, int R, int h, const Tin* __restrict__ a, const Tin* __restrict__ b,
              const Tin* __restrict__ c, const Tin* __restrict__ d, Tin* __restrict__ x, float tol,
-             unsigned* __restrict__ bound_max, int* __restrict__ status, int vec16) {
+             unsigned* __restrict__ bound_max, int* __restrict__ status, int vec16,
+             unsigned* __restrict__ dmax) {
   using T = typename Ar::T;
   using Lay = WinLayout<Ar, Tin>;
   static_assert(sizeof(T) <= sizeof(Tin), "relations are stored in the input slots");
@@ -514,10 +542,11 @@ __global__ void __launch_bounds__(kWinThreads)
   if (p > 1 && E - (p - 1) * mt == 1) --p;  // merge a one-row tail
   bool bad = false;
   T red[8];
+  RowChk chk;
   const int myL = tid < p ? (tid == p - 1 ? E - tid * mt : mt) : 0;
   if (tid < p) {
     const AccL0<Ar, Tin> A{{s0[0], s0[1], s0[2], s0[3]}, tid * mt};
-    oc_fwd<Ar>(A, myL, red, bad);
+    oc_fwd<Ar>(A, myL, red, bad, chk);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       lv[q][lvx(2 * tid)] = red[q];
@@ -525,12 +554,17 @@ __global__ void __launch_bounds__(kWinThreads)
     }
   }
   __syncthreads();
+  // the rows' range (the system-wide |d / b| test runs after the launch)
+  if (dmax) codes_raise_warp(dmax, 0, true, chk);
+  if (chk.range_bad()) atomicOr(status, ST_RANGE);
+  bad |= chk.b_bad();
   OcLevels lev;
   oc_reduce_levels<Ar>(lv, 2 * p, tid, lev, bad);
   // ---- the window's two interface equations, with nothing outside: a 2x2 system
   if (tid == 0) {
     const AccLv<Ar> A{{lv[0], lv[1], lv[2], lv[3]}, lev.off};
-    oc_fwd<Ar>(A, lev.N, red, bad);
+    RowChk nochk;
+    oc_fwd<Ar>(A, lev.N, red, bad, nochk);
     // b1 f + c1 l = d1;  a2 f + b2 l = d2
     const T det = Ar::sub_mul(Ar::mul(red[1], red[5]), red[2], red[4]);
     bad |= Ar::bad_pivot(det);
@@ -557,6 +591,9 @@ __global__ void __launch_bounds__(kWinThreads)
     *reinterpret_cast<float4*>(x + k0 + i * V) =
         *reinterpret_cast<const float4*>(s0[3] + o + i * V);
   for (int i = kv * V + tid; i < K; i += kWinThreads) x[k0 + i] = s0[3][o + i];
+  bool oob = false;
+  for (int i = tid; i < K; i += kWinThreads) oob |= Ar::out_bad(s0[3][o + i]);
+  if (oob) atomicOr(status, ST_RANGE);
 
   // ---- the window's truncation bound
   if (tid == 0) {

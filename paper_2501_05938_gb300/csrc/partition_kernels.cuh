@@ -59,6 +59,10 @@ struct Level {
   int32_t llast;    // length of block p-1, in [2, m+1]
   int32_t ncap;     // checkpoint slots per block
   int32_t pad;
+  // level 0 of fp64 inputs in narrower arithmetic: per system (nbnd + 1
+  // of them) the kCodes range codes of its rows (RowChk), raised by Stage 1
+  // with atomicMax; null elsewhere
+  unsigned* dmax;
 };
 
 __device__ __forceinline__ int block_len(const Level& lv, int64_t k) {
@@ -109,7 +113,52 @@ struct Bounds {
 };
 
 // Status bits written into the device status word.
-enum : int { ST_BAD_PIVOT = 1, ST_NO_CONVERGENCE = 2, ST_TIMEOUT = 4 };
+enum : int { ST_BAD_PIVOT = 1, ST_NO_CONVERGENCE = 2, ST_TIMEOUT = 4, ST_RANGE = 8 };
+
+// Range codes of packed systems: three words per system (RowChk's dcode,
+// ecode, fcode maxima).  Raise system `sys`'s codes to v (an atomic only
+// where that would change a code; the entries are read from L2).
+constexpr int kCodes = 3;
+__device__ __forceinline__ void code_raise(unsigned* p, unsigned v) {
+  if (v != 0u && __ldcg(p) < v) atomicMax(p, v);
+}
+__device__ __forceinline__ void codes_raise(unsigned* dmax, int64_t sys, unsigned dc,
+                                            unsigned ec, unsigned fc) {
+  unsigned* p = dmax + kCodes * sys;
+  code_raise(p, dc);
+  code_raise(p + 1, ec);
+  code_raise(p + 2, fc);
+}
+// The warp's codes: one set of atomics per warp where every lane is in the
+// same system (always for a single system), else per lane.
+__device__ __forceinline__ void codes_raise_warp(unsigned* dmax, int64_t sys, bool active,
+                                                 const RowChk& k) {
+  const unsigned dc = active ? k.dcode() : 0u, ec = active ? k.ecode : 0u,
+                 fc = active ? k.fcode() : 0u;
+  const int64_t sys0 = __shfl_sync(0xffffffffu, sys, 0);
+  if (__all_sync(0xffffffffu, !active || sys == sys0)) {
+    const unsigned wd = __reduce_max_sync(0xffffffffu, dc);
+    const unsigned we = __reduce_max_sync(0xffffffffu, ec);
+    const unsigned wf = __reduce_max_sync(0xffffffffu, fc);
+    if ((threadIdx.x & 31) == 0) codes_raise(dmax, sys0, wd, we, wf);
+  } else if (active) {
+    codes_raise(dmax, sys, dc, ec, fc);
+  }
+}
+
+// After every row of the level-0 system has been loaded: flag ST_RANGE for
+// each system whose codes are out of range (range_codes_bad), and clear the
+// codes for the next solve.  One CTA.
+static __global__ void __launch_bounds__(256)
+    k_dcode_check(unsigned* __restrict__ dmax, int64_t count, int* __restrict__ status) {
+  bool bad = false;
+  for (int64_t i = threadIdx.x; i < count; i += blockDim.x) {
+    unsigned* p = dmax + kCodes * i;
+    bad |= range_codes_bad(p[0], p[1], p[2]);
+    p[0] = p[1] = p[2] = 0u;
+  }
+  if (bad) atomicOr(status, ST_RANGE);
+}
 
 // ------------------------------------------------------------------ cp.async
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -311,6 +360,10 @@ __global__ void __launch_bounds__(W * 32)
   T a0 = Ar::zero(), b0 = Ar::one(), c0 = Ar::zero(), d0 = Ar::zero();
   T beta = Ar::one(), clast = Ar::zero();
   bool bad = false;
+  // range of the rows (fp64 inputs in narrower arithmetic), and the packed
+  // system the current row belongs to (for its |d / b| code)
+  RowChk chk;
+  int64_t sys = lv.nbnd > 0 && active ? bd.first : 0;
 
   // one interior row (1 <= row <= L-2).  The product chains alpha and S and
   // the accumulators P and Q are left unnormalised here and renormalised
@@ -366,8 +419,11 @@ __global__ void __launch_bounds__(W * 32)
 #pragma unroll
         for (int v = 0; v < V; ++v) {
           const int rr = r + v;
-          const T av = Ar::from(xa.v[v]), bv = Ar::from_pivot(xb.v[v]), cv = Ar::from(xc.v[v]),
-                  dv = Ar::from(xd.v[v]);
+          // a of the system's first row and c of its last are never read
+          const Tin ain = (rr == 0 && first && k == 0) ? Tin{} : xa.v[v];
+          const Tin cin = (rr == R - 1 && last && k == lv.p - 1) ? Tin{} : xc.v[v];
+          T av, bv, cv, dv;
+          Ar::template row<true>(ain, xb.v[v], cin, xd.v[v], av, bv, cv, dv, chk);
           if (rr == 0 && first) {  // the block's first row: f's equation
             a0 = av; b0 = bv; c0 = cv; d0 = dv;
           } else if (rr == R - 1 && last) {  // the block's last row
@@ -389,12 +445,21 @@ __global__ void __launch_bounds__(W * 32)
       for (int r = 0; r < R; ++r) {
         const int row = row0 + r;
         if (row < L) {
-          T av = Ar::from(t[r]), cv = Ar::from(t[2 * TL::kArr + r]);
-          const T bv = Ar::from_pivot(t[TL::kArr + r]), dv = Ar::from(t[3 * TL::kArr + r]);
-          if (bd.cnt > 0) {  // couplings cut at system boundaries
-            if (bd.is(start + row)) av = Ar::zero();
-            if (bd.is(start + row + 1)) cv = Ar::zero();
+          // couplings cut at system boundaries (and a[0], c[n-1]) are never read
+          bool cut_a = k == 0 && row == 0, cut_c = k == lv.p - 1 && row == L - 1;
+          if (bd.cnt > 0) {
+            if (bd.is(start + row)) {  // a new packed system starts here
+              cut_a = true;
+              if (lv.dmax) codes_raise(lv.dmax, sys, chk.dcode(), chk.ecode, chk.fcode());
+              chk.reset_codes();
+              ++sys;
+            }
+            cut_c |= bd.is(start + row + 1);
           }
+          T av, bv, cv, dv;
+          Ar::template row<true>(cut_a ? Tin{} : t[r], t[TL::kArr + r],
+                                 cut_c ? Tin{} : t[2 * TL::kArr + r], t[3 * TL::kArr + r], av, bv,
+                                 cv, dv, chk);
           if (row == 0) {
             a0 = av; b0 = bv; c0 = cv; d0 = dv;
           } else if (row < L - 1) {
@@ -443,8 +508,10 @@ __global__ void __launch_bounds__(W * 32)
       Ar::to(rc[2 * k + 1], k == lv.p - 1 ? Ar::zero() : clast);
       Ar::to(rd[2 * k + 1], g);
     }
-    if (bad) atomicOr(status, ST_BAD_PIVOT);
+    if (bad || chk.b_bad()) atomicOr(status, ST_BAD_PIVOT);
+    if (chk.range_bad()) atomicOr(status, ST_RANGE);
   }
+  if (lv.dmax) codes_raise_warp(lv.dmax, sys, active, chk);
 }
 
 // ------------------------------------------------------------------ Stage 3
@@ -503,7 +570,8 @@ __global__ void __launch_bounds__(W * 32)
     l = Ar::from(xred[2 * k + 1]);
   }
   T xnext = l;  // x of the row below the chunk being processed
-  bool bad = false;
+  bool bad = false, oob = false;
+  RowChk nochk;  // the rows' range was checked by Stage 1
 
   // chunks bottom-up: ch = nch-1 .. 0; buffer parity follows the visiting order
   for (int it = 0; it < nch; ++it) {
@@ -543,26 +611,33 @@ __global__ void __launch_bounds__(W * 32)
         for (int v = 0; v < V; ++v) {
           const int rr = r + v;
           if ((rr == 0 && first) || (rr == R - 1 && last)) continue;
-          const T av = Ar::from(xa.v[v]);
-          const T beta = Ar::sub_mul_dom(Ar::from(xb.v[v]), av, gp);
+          T av, bv, cv, dv;
+          Ar::template row<false>(xa.v[v], xb.v[v], xc.v[v], xd.v[v], av, bv, cv, dv, nochk);
+          const T beta = Ar::sub_mul_dom(bv, av, gp);
           bad |= Ar::bad_pivot(beta);
           const T rbeta = Ar::rcp(beta);
-          zp = Ar::mul_nn(Ar::sub_mul(Ar::from(xd.v[v]), av, zp), rbeta);
-          gp = Ar::mul_nn(Ar::from(xc.v[v]), rbeta);
+          zp = Ar::mul_nn(Ar::sub_mul(dv, av, zp), rbeta);
+          gp = Ar::mul_nn(cv, rbeta);
           Z[rr] = zp;
           G[rr] = gp;
         }
       }
+      // back-substitution (x over the Z slots), then the output conversion
 #pragma unroll
       for (int r = R - 1; r >= 0; --r) {
         if (r == R - 1 && last) {
-          Ar::to(xo[r], l);  // xnext is l already
+          Z[r] = l;  // xnext is l already
         } else if (r == 0 && first) {
-          Ar::to(xo[r], f);
+          Z[r] = f;
         } else {
           xnext = Ar::sub_mul(Z[r], G[r], xnext);
-          Ar::to(xo[r], xnext);
+          Z[r] = xnext;
         }
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        Ar::to(xo[r], Z[r]);
+        oob |= Ar::out_bad(xo[r]);
       }
 #pragma unroll
       for (int r = 0; r < R; r += V) {
@@ -580,15 +655,17 @@ __global__ void __launch_bounds__(W * 32)
       for (int r = 0; r < R; ++r) {
         const int row = row0 + r;
         if (row >= 1 && row <= L - 2) {
-          T av = Ar::from(t[r]), cv = Ar::from(t[2 * TL::kArr + r]);
+          T av, bv, cv, dv;
+          Ar::template row<false>(t[r], t[TL::kArr + r], t[2 * TL::kArr + r],
+                                  t[3 * TL::kArr + r], av, bv, cv, dv, nochk);
           if (bd.cnt > 0) {  // couplings cut at system boundaries
             if (bd.is(start + row)) av = Ar::zero();
             if (bd.is(start + row + 1)) cv = Ar::zero();
           }
-          const T beta = Ar::sub_mul_dom(Ar::from(t[TL::kArr + r]), av, gp);
+          const T beta = Ar::sub_mul_dom(bv, av, gp);
           bad |= Ar::bad_pivot(beta);
           const T rbeta = Ar::rcp(beta);
-          zp = Ar::mul_nn(Ar::sub_mul(Ar::from(t[3 * TL::kArr + r]), av, zp), rbeta);
+          zp = Ar::mul_nn(Ar::sub_mul(dv, av, zp), rbeta);
           gp = Ar::mul_nn(cv, rbeta);
           zs[r] = zp;
           gs[r] = gp;
@@ -608,6 +685,7 @@ __global__ void __launch_bounds__(W * 32)
             xnext = xr;
           }
           Ar::to(t[r], xr);
+          oob |= Ar::out_bad(t[r]);
         }
       }
     }
@@ -617,6 +695,7 @@ __global__ void __launch_bounds__(W * 32)
     __syncwarp();  // the buffer is refilled by the next iteration's copies
   }
   if (active && bad) atomicOr(status, ST_BAD_PIVOT);
+  if (active && oob) atomicOr(status, ST_RANGE);
 }
 
 // ------------------------------------------------------------------ small systems
@@ -626,34 +705,41 @@ __global__ void __launch_bounds__(W * 32)
 // x_i = d_i / b_i.  Rows outside [0, n) act as identity rows.
 constexpr int kBaseMax = 64;
 
+// dmax (level 0 of fp64 inputs in narrower arithmetic, else null): the
+// per-system range codes, raised here; x is checked for range.
 template <class Ar, class Tin, class Tout>
 __global__ void __launch_bounds__(32)
     k_base(int64_t n, const Tin* __restrict__ a, const Tin* __restrict__ b,
            const Tin* __restrict__ c, const Tin* __restrict__ d, Tout* __restrict__ x,
-           const int64_t* __restrict__ bnd, int64_t nbnd, int* __restrict__ status) {
+           const int64_t* __restrict__ bnd, int64_t nbnd, int* __restrict__ status,
+           unsigned* __restrict__ dmax) {
   using T = typename Ar::T;
   __shared__ T sa[kBaseMax], sb[kBaseMax], sc[kBaseMax], sd[kBaseMax];
   const int lane = threadIdx.x;
   const int nn = (int)n;
+  bool bad = false, oob = false;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int i = lane + 32 * h;
     if (i < nn) {
       bool start = (i == 0), end = (i == nn - 1);
+      int64_t sys = 0;
       for (int64_t j = 0; j < nbnd; ++j) {  // packed systems: cut the couplings
         start |= bnd[j] == i;
         end |= bnd[j] == i + 1;
+        sys += bnd[j] <= i;
       }
-      sa[i] = start ? Ar::zero() : Ar::from(a[i]);
-      sb[i] = Ar::from(b[i]);
-      sc[i] = end ? Ar::zero() : Ar::from(c[i]);
-      sd[i] = Ar::from(d[i]);
+      RowChk rc;
+      Ar::template row<true>(start ? Tin{} : a[i], b[i], end ? Tin{} : c[i], d[i], sa[i], sb[i],
+                             sc[i], sd[i], rc);
+      oob |= rc.range_bad();
+      bad |= rc.b_bad();
+      if (dmax) codes_raise(dmax, sys, rc.dcode(), rc.ecode, rc.fcode());
     } else {
       sa[i] = Ar::zero(); sb[i] = Ar::one(); sc[i] = Ar::zero(); sd[i] = Ar::zero();
     }
   }
   __syncwarp();
-  bool bad = false;
   for (int s = 1; s < nn; s <<= 1) {
     T na[2], nbv[2], nc[2], nd[2];
 #pragma unroll
@@ -689,10 +775,14 @@ __global__ void __launch_bounds__(32)
     const int i = lane + 32 * h;
     if (i < nn) {
       bad |= Ar::bad_pivot(sb[i]);
-      Ar::to(x[i], Ar::mul(sd[i], Ar::rcp(sb[i])));
+      Tout xv;
+      Ar::to(xv, Ar::mul(sd[i], Ar::rcp(sb[i])));
+      oob |= Ar::out_bad(xv);
+      x[i] = xv;
     }
   }
   if (bad) atomicOr(status, ST_BAD_PIVOT);
+  if (oob) atomicOr(status, ST_RANGE);
 }
 
 }  // namespace tps

@@ -75,7 +75,7 @@ template <class Ar, class Tin>
 static cudaError_t launch_onchip_raw(int64_t n, const Tin* a, const Tin* b, const Tin* c,
                                      const Tin* d, Tin* x, void* xch_bytes, unsigned* bar,
                                      int* status, bool extra_arrival, cudaStream_t s,
-                                     bool& used) {
+                                     bool& used, unsigned* dmax) {
   used = false;
   OcGeom g;
   if (!oc_geometry<Tin>(n, oc_ctas_max<Ar, Tin>(), g)) return cudaSuccess;
@@ -97,20 +97,33 @@ static cudaError_t launch_onchip_raw(int64_t n, const Tin* a, const Tin* b, cons
   cfg.numAttrs = 1;
   const unsigned arrivals = (unsigned)g.G + (extra_arrival ? 1u : 0u);
   e = cudaLaunchKernelEx(&cfg, k_onchip<Ar, Tin>, n, g.mt, g.p, a, b, c, d, x, xch, bar,
-                         arrivals, status, vec16);
+                         arrivals, status, vec16, dmax);
   if (e == cudaSuccess) used = true;
   return e;
 }
 
+// dmax: the |d / b| codes where this is level 0 (level0_dmax), else null.
 template <class Ar, class Tin>
 static cudaError_t launch_onchip(tps_plan_s* P, int64_t n, const Tin* a, const Tin* b,
                                  const Tin* c, const Tin* d, Tin* x, cudaStream_t s,
-                                 bool& used) {
+                                 bool& used, unsigned* dmax) {
   used = false;
   if (P->desc.flags & TPS_NO_ONCHIP) return cudaSuccess;
   return launch_onchip_raw<Ar, Tin>(n, a, b, c, d, x, P->ws + P->off_xch,
                                     reinterpret_cast<unsigned*>(P->ws + 32), P->d_status,
-                                    P->test_barrier_extra, s, used);
+                                    P->test_barrier_extra, s, used, dmax);
+}
+
+unsigned* level0_dmax(tps_plan_s* P) {
+  return P->desc.dtype == TPS_F64_DF ? reinterpret_cast<unsigned*>(P->ws + P->off_dmax)
+                                     : nullptr;
+}
+
+cudaError_t dcode_check(tps_plan_s* P, int64_t count, cudaStream_t s) {
+  unsigned* dmax = level0_dmax(P);
+  if (!dmax) return cudaSuccess;
+  k_dcode_check<<<1, 256, 0, s>>>(dmax, count, P->d_status);
+  return cudaGetLastError();
 }
 
 Level make_level(int64_t n, int m, int R) {
@@ -258,11 +271,11 @@ static cudaError_t run_levels(tps_plan_s* P, const std::vector<LevelPlan>& level
                               Tin* x, cudaStream_t s) {
   if (idx == levels.size()) {
     if (n <= 0) return cudaSuccess;
-    k_base<Ar, Tin, Tin><<<1, 32, 0, s>>>(n, a, b, c, d, x, nullptr, 0, P->d_status);
+    k_base<Ar, Tin, Tin><<<1, 32, 0, s>>>(n, a, b, c, d, x, nullptr, 0, P->d_status, nullptr);
     return cudaGetLastError();
   }
   bool used = false;
-  cudaError_t eo = launch_onchip<Ar, Tin>(P, n, a, b, c, d, x, s, used);
+  cudaError_t eo = launch_onchip<Ar, Tin>(P, n, a, b, c, d, x, s, used, nullptr);
   if (eo != cudaSuccess || used) {
     if (used) {
       P->last_onchip = 2;
@@ -351,6 +364,7 @@ cudaError_t stage1_range(tps_plan_s* P, const LevelPlan& L, int64_t kb, int64_t 
     Level lv = L.lv;
     lv.k_begin = kb;
     lv.k_end = ke;
+    lv.dmax = level0_dmax(P);
     Tred* red[4];
     for (int i = 0; i < 4; ++i) red[i] = reinterpret_cast<Tred*>(P->ws + L.off_red[i]);
     Tred* ck[3];
@@ -405,7 +419,8 @@ cudaError_t base_solve(tps_plan_s* P, int64_t n, const void* a, const void* b, c
     using Tin = std::remove_pointer_t<decltype(tin)>;
     (void)tred;
     k_base<Ar, Tin, Tin><<<1, 32, 0, s>>>(n, (const Tin*)a, (const Tin*)b, (const Tin*)c,
-                                          (const Tin*)d, (Tin*)x, bnd, nbnd, P->d_status);
+                                          (const Tin*)d, (Tin*)x, bnd, nbnd, P->d_status,
+                                          level0_dmax(P));
     return cudaGetLastError();
   });
 }
@@ -525,7 +540,7 @@ static tps_status run_solve_direct(tps_plan_s* P, int64_t n, const void* a, cons
       using Tin = std::remove_pointer_t<decltype(tin)>;
       (void)tred;
       return launch_onchip<Ar, Tin>(P, n, (const Tin*)a, (const Tin*)b, (const Tin*)c,
-                                    (const Tin*)d, (Tin*)x, s, onchip);
+                                    (const Tin*)d, (Tin*)x, s, onchip, level0_dmax(P));
     });
     if (onchip) {
       P->last_onchip = 1;
@@ -537,9 +552,11 @@ static tps_status run_solve_direct(tps_plan_s* P, int64_t n, const void* a, cons
   } else if (lv.empty()) {
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
     if (e == cudaSuccess) e = base_solve(P, n, a, b, c, d, x, s, bnd, nbnd);
+    if (e == cudaSuccess) e = dcode_check(P, nbnd + 1, s);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
   } else {
     if (e == cudaSuccess) e = stage1_range(P, lv[0], 0, lv[0].lv.p, a, b, c, d, s);
+    if (e == cudaSuccess) e = dcode_check(P, nbnd + 1, s);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
     // with stage events (TPS_TRACE) TPS_GRAPH captures Stage 2 alone; without
     // them the whole solve is one graph already (run_solve_graph)
@@ -569,7 +586,7 @@ static cudaError_t launch_window(tps_plan_s* P, int64_t n, const Tin* a, const T
   if (e != cudaSuccess) return e;
   const float tol = (float)(P->desc.tol > 0.0 ? P->desc.tol : 1e-12);
   k_window<Ar, Tin><<<(unsigned)windows, kWinThreads, smem, s>>>(
-      n, R, h, a, b, c, d, x, tol, bound, P->d_status, (al % 16) == 0);
+      n, R, h, a, b, c, d, x, tol, bound, P->d_status, (al % 16) == 0, level0_dmax(P));
   return cudaGetLastError();
 }
 
@@ -589,19 +606,21 @@ tps_status run_truncated(tps_plan_s* P, int64_t n, const void* a, const void* b,
                                     (const Tin*)d, (Tin*)x, s);
     });
   }
+  if (e == cudaSuccess) e = dcode_check(P, 1, s);
   return e == cudaSuccess ? TPS_OK : TPS_ERR_CUDA;
 }
 
 
 cudaError_t onchip_solve(int dtype, int64_t n, const void* a, const void* b, const void* c,
                          const void* d, void* x, void* xch, unsigned* bar, int* status,
-                         cudaStream_t s, bool& used) {
+                         cudaStream_t s, bool& used, unsigned* dmax) {
   return dispatch(dtype, [&](auto ar, auto* tin, auto* tred) -> cudaError_t {
     using Ar = decltype(ar);
     using Tin = std::remove_pointer_t<decltype(tin)>;
     (void)tred;
     return launch_onchip_raw<Ar, Tin>(n, (const Tin*)a, (const Tin*)b, (const Tin*)c,
-                                      (const Tin*)d, (Tin*)x, xch, bar, status, false, s, used);
+                                      (const Tin*)d, (Tin*)x, xch, bar, status, false, s, used,
+                                      dmax);
   });
 }
 

@@ -77,6 +77,8 @@ static void default_params(const tps_plan_desc& d, int32_t& m, int32_t& mr, int3
 static size_t workspace_for(tps_plan_s* P, size_t* off_levels_out, size_t* off_dev_out) {
   size_t off = 0;
   off = align_up(off + 64);  // status word, refinement maxima, grid-barrier counter
+  P->off_dmax = off;         // per-system range codes (zero between solves)
+  off = align_up(off + 4 * kCodes * (size_t)std::max<int64_t>(1, P->desc.batch_max));
   P->off_xch = off;          // interface rows of the on-chip solve
   off = align_up(off + onchip_exchange_bytes());
   *off_levels_out = off;
@@ -121,6 +123,7 @@ const char* tps_status_string(tps_status s) {
     case TPS_ERR_ZERO_PIVOT: return "zero or non-finite pivot";
     case TPS_ERR_NO_CONVERGENCE: return "refinement did not converge";
     case TPS_ERR_TIMEOUT: return "device wait timed out";
+    case TPS_ERR_RANGE: return "value outside the range of the arithmetic";
   }
   return "unknown status";
 }
@@ -259,7 +262,7 @@ tps_status tps_plan(const tps_plan_desc* desc, tps_plan_t* out) {
     P->ws_owned = true;
     P->d_status = (int*)P->ws;
     P->d_scalars = (double*)(P->ws + 8);
-    e = cudaMemset(P->ws, 0, 64);
+    e = cudaMemset(P->ws, 0, P->off_xch);  // header and range codes
     if (e != cudaSuccess) {
       tps_plan_destroy(P);
       return TPS_ERR_CUDA;
@@ -341,7 +344,7 @@ tps_status tps_set_workspace(tps_plan_t P, void* dev_ptr, size_t bytes) {
   P->ws_owned = false;
   P->d_status = (int*)P->ws;
   P->d_scalars = (double*)(P->ws + 8);
-  return cudaMemset(P->ws, 0, 64) == cudaSuccess ? TPS_OK : TPS_ERR_CUDA;
+  return cudaMemset(P->ws, 0, P->off_xch) == cudaSuccess ? TPS_OK : TPS_ERR_CUDA;
 }
 
 }  // extern "C"
@@ -509,6 +512,7 @@ tps_status tps_solve_host_async(tps_plan_t P, int64_t n, const void* a, const vo
       e = copy(dev[i], host[i], (size_t)n * es, cudaMemcpyHostToDevice, s0);
     if (e == cudaSuccess) e = cudaEventRecord(H->ev_up, s0);
     if (e == cudaSuccess) e = base_solve(P, n, dev[0], dev[1], dev[2], dev[3], dev[4], s0);
+    if (e == cudaSuccess) e = dcode_check(P, 1, s0);
     if (e == cudaSuccess)
       e = copy((void*)host[4], dev[4], (size_t)n * es, cudaMemcpyDeviceToHost, s0);
     if (e == cudaSuccess) e = cudaEventRecord(H->ev_done3[0], s0);
@@ -545,6 +549,7 @@ tps_status tps_solve_host_async(tps_plan_t P, int64_t n, const void* a, const vo
     if (e == cudaSuccess && i > 0) e = cudaStreamWaitEvent(H->streams[0], H->ev_done1[i], 0);
   }
   if (e == cudaSuccess) e = cudaEventRecord(H->ev_up, H->streams[0]);
+  if (e == cudaSuccess) e = dcode_check(P, 1, H->streams[0]);
   if (e == cudaSuccess)
     e = (P->desc.flags & TPS_GRAPH) ? reduced_solve_graph(P, lv, H->streams[0])
                                     : reduced_solve(P, lv, H->streams[0]);
@@ -791,6 +796,7 @@ tps_status tps_plan_query(tps_plan_t P, tps_info* out) {
   int32_t status = TPS_OK;
   if (word & ST_BAD_PIVOT) status = TPS_ERR_ZERO_PIVOT;
   else if (word & ST_TIMEOUT) status = TPS_ERR_TIMEOUT;
+  else if (word & ST_RANGE) status = TPS_ERR_RANGE;
   else if ((word & ST_NO_CONVERGENCE) || P->host_status == TPS_ERR_NO_CONVERGENCE)
     status = TPS_ERR_NO_CONVERGENCE;
   P->host_status = TPS_OK;

@@ -68,6 +68,9 @@ struct tps_plan_s {
   size_t ws_bytes = 0, ws_needed = 0;
   bool ws_owned = false;
   int* d_status = nullptr;     // device status word (first bytes of ws)
+  // per-system range codes of the last solve's rows (double-float plans;
+  // kCodes x max(1, batch_max) words after the header), zero between solves
+  size_t off_dmax = 0;
   double* d_scalars = nullptr; // refinement reductions (next bytes of ws)
   size_t off_levels = 0;       // first level buffer offset
   size_t off_refine = 0;       // refinement residual and correction vectors
@@ -143,10 +146,11 @@ size_t onchip_exchange_bytes();
 // The single-launch on-chip solve of one system if it fits on this device
 // (used = true), else nothing.  xch: onchip_exchange_bytes() of device
 // memory; bar: a device counter (zeroed by the call); status: the device
-// status word.
+// status word; dmax: for double-float, one system's kCodes range codes,
+// zero before the launch and left zero after it (else null).
 cudaError_t onchip_solve(int dtype, int64_t n, const void* a, const void* b, const void* c,
                          const void* d, void* x, void* xch, unsigned* bar, int* status,
-                         cudaStream_t s, bool& used);
+                         cudaStream_t s, bool& used, unsigned* dmax);
 // TPS_TRUNCATE: the windowed solve of one device-resident system.
 tps_status run_truncated(tps_plan_s* P, int64_t n, const void* a, const void* b, const void* c,
                          const void* d, void* x, cudaStream_t s);
@@ -162,6 +166,12 @@ cudaError_t reduced_solve_graph(tps_plan_s* P, const std::vector<LevelPlan>& lev
 cudaError_t base_solve(tps_plan_s* P, int64_t n, const void* a, const void* b, const void* c,
                        const void* d, void* x, cudaStream_t s, const int64_t* bnd = nullptr,
                        int64_t nbnd = 0);
+// The per-system range codes that level 0 of this plan's solves raises
+// (null where the arithmetic needs no such test).
+unsigned* level0_dmax(tps_plan_s* P);
+// After level 0 has loaded every row: flag ST_RANGE for each of `count`
+// systems whose range codes are out of range, and clear the codes.
+cudaError_t dcode_check(tps_plan_s* P, int64_t count, cudaStream_t s);
 
 // Mixed-precision refinement of one device-resident system (or packed
 // systems): fp32 partition elimination, fp64 residual and update.  Reads two

@@ -1,20 +1,27 @@
 """tps_solve_noalloc: the allocation-free solve for callers that may not call
 cudaMalloc (a framework allocator that owns all device memory, a fixed
 device-memory budget, latency-critical loops).  Its result must agree with the
-ordinary plan-based tps_solve, and two calls in a row must both be right
-even though they share the library's fixed scratch array.  This file is
-named so that pytest collects it last."""
+ordinary plan-based tps_solve and with the CPU oracle, and two calls in a row
+must both be right even though they share the library's fixed scratch array.
+Both of its routes are run: the single-launch on-chip solve it takes for
+every accepted size on a GB300, and the level-by-level route it keeps for
+devices where that launch does not fit (forced here by a test switch).  This
+file is named so that pytest collects it last."""
 import ctypes
 
+import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle
 from paper_2501_05938_gb300 import binding, synth
 
 pytestmark = pytest.mark.gpu
 
 TOL = {"f64": 1e-10, "f64_df": 1e-10, "f32": 1e-5}
+# against the fp64 oracle: (forward error, residual); fp32 on the fp32-rounded inputs
+ORACLE_TOL = {"f64": (1e-10, 1e-12), "f64_df": (1e-10, 1e-12), "f32": (1e-5, 1e-5)}
 
 
 def noalloc_fn():
@@ -31,17 +38,18 @@ def rel(x, y):
     return ((x - y).abs().max() / y.abs().max()).item()
 
 
-@pytest.mark.parametrize("dtype", ["f64_df", "f64", "f32"])
-def test_noalloc_matches_tps_solve_on_two_calls(dtype):
+def check_two_calls(dtype):
+    """Two calls in a row (the largest size, then a ragged one), each against
+    the plan-based tps_solve on its level-by-level route and the oracle."""
     f = noalloc_fn()
     tdt = torch.float32 if dtype == "f32" else torch.float64
     stream = torch.cuda.current_stream()
-    for seed, n in ((21, 262144), (22, 100003)):  # the largest size, then a ragged one
+    for seed, n in ((21, 262144), (22, 100003)):
         s = synth.system(seed, n)
+        if dtype == "f32":
+            s = synth.to_f32(s)
         a, b, c, d = (torch.as_tensor(s[k]).to("cuda", tdt) for k in "abcd")
         x_ref = torch.empty_like(b)
-        # the plan-based solve on the level-by-level route (the no-alloc call
-        # takes the on-chip route at these sizes): two independent routes
         binding.Plan(n, dtype=dtype, m=64, m_reduced=32,
                      flags=binding.NO_ONCHIP).solve(a, b, c, d, x_ref)
         x = torch.full_like(b, float("nan"))
@@ -52,6 +60,25 @@ def test_noalloc_matches_tps_solve_on_two_calls(dtype):
         torch.cuda.synchronize()
         assert st.item() == 0
         assert rel(x, x_ref) <= TOL[dtype]
+        s64 = {k: np.asarray(s[k], dtype=np.float64) for k in "abcd"}
+        ref = oracle.thomas(s64["a"], s64["b"], s64["c"], s64["d"])
+        xs = x.cpu().numpy().astype(np.float64)
+        fwd, res = ORACLE_TOL[dtype]
+        assert oracle.rel_forward_error(xs, ref) <= fwd
+        assert oracle.rel_residual(s64["a"], s64["b"], s64["c"], s64["d"], xs) <= res
+
+
+@pytest.mark.parametrize("dtype", ["f64_df", "f64", "f32"])
+def test_noalloc_matches_tps_solve_on_two_calls(dtype):
+    check_two_calls(dtype)
+
+
+@pytest.mark.parametrize("dtype", ["f64_df", "f64", "f32"])
+def test_noalloc_level_route_on_two_calls(dtype, monkeypatch):
+    # the route whose reduced systems and checkpoints live in the shared
+    # scratch array; the switch is read on every call
+    monkeypatch.setenv("TPS_TEST_NOALLOC_LEVELS", "1")
+    check_two_calls(dtype)
 
 
 def test_noalloc_rejects_sizes_beyond_its_maximum():
