@@ -49,6 +49,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -108,6 +110,26 @@ def traffic_table():
                 if hsh == kernel_source_hash():
                     out[k] = float(v)
     return out
+
+
+def fp64_table():
+    """fp64-pipe thread instructions per row of each plain (native fp64)
+    kernel from the committed ncu summary, used only while the kernel
+    sources still hash to what was profiled."""
+    out = {}
+    path = os.path.join(ROOT, "profiles", "fp64_pipe_per_row.txt")
+    if os.path.exists(path):
+        with open(path) as f:
+            for line in f:
+                if line.startswith("#") or not line.strip():
+                    continue
+                k, v, hsh = line.split()[:3]
+                if hsh == kernel_source_hash():
+                    out[k] = float(v)
+    return out
+
+
+GATE_FWD, GATE_RES = 1e-10, 1e-12  # the fp64 bar: forward error vs the oracle, residual
 
 
 class Clocks:
@@ -300,7 +322,8 @@ def verify(g, x):
 
 def cpu_oracle_leg(g, x_gpu, budget_s=12.0):
     """The serial Thomas oracle on the full system; returns the throughput
-    and the GPU result's relative forward error against it."""
+    and the GPU result's relative forward error against it; beside it the
+    partition method with Stages 1 and 3 over every host core."""
     import oracle
 
     a, b, c, d = (g[k].cpu().numpy() for k in "abcd")
@@ -326,12 +349,25 @@ def cpu_oracle_leg(g, x_gpu, budget_s=12.0):
         t0 = time.perf_counter()
         oracle.partition(a[:k], b[:k], c[:k], d[:k], 128)
         tp.append(time.perf_counter() - t0)
+    # the multi-core baseline: the partition method with Stages 1 and 3 over
+    # one thread per host core (Stage 2 serial), the full system, best of 3
+    cores = os.cpu_count() or 1
+    tt = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        oracle.partition_threaded(a, b, c, d, 128, threads=cores)
+        tt.append(time.perf_counter() - t0)
     return {"value": n / best, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"serial fp64 Thomas oracle on the full n={n} system, best of "
                       f"{len(times)} solves ({sum(times):.1f} s of CPU work)",
             "partition_value": k / min(tp),
             "partition_sample": f"serial fp64 partition oracle (m = 128), best of 3 solves "
-                                f"of the first {k} rows"}, err, res, ref
+                                f"of the first {k} rows",
+            "threaded": {"value": n / min(tt), "unit": UNIT, "cores": cores,
+                         "kind": "oracle (partition, Stages 1 and 3 threaded)",
+                         "sample": f"fp64 partition solve (m = 128) of the full n={n} system "
+                                   f"with Stages 1 and 3 over {cores} threads (nproc), "
+                                   f"Stage 2 serial; best of 3"}}, err, res, ref
 
 
 def workload_name(n):
@@ -349,7 +385,7 @@ def reference_arm(a):
     import oracle
     from paper_2501_05938_gb300 import synth
 
-    n = min(a.n, 1 << 23)  # a bounded sample of the workload per step
+    n = a.n  # the workload itself: one step = one serial solve (~1.3 s at n = 2^27)
     s = synth.system(SEED, n)
     oracle.build()
     for _ in range(a.warmup):
@@ -359,9 +395,8 @@ def reference_arm(a):
         oracle.thomas(s["a"], s["b"], s["c"], s["d"])
     dt = (time.perf_counter() - t0) / a.steps
     v = n / dt
-    sample = (f"serial fp64 Thomas oracle; one step = one solve of an n={n} system from the "
-              f"same generator (a bounded sample of the n={a.n} workload; unknowns/s scale "
-              f"linearly with n for this serial O(n) solver)")
+    sample = (f"serial fp64 Thomas oracle on one host core; one step = one solve of the "
+              f"n={n} workload system (same generator and seed)")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -373,6 +408,89 @@ def reference_arm(a):
                              "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def mixed_workloads(binding, synth, world, rank, stream, a):
+    """The refinement workload (FP32 elimination, FP64 residual and update):
+    one n = 2^27 system at dominance ratios b / (|a| + |c|) of 1.01, 1.1 and
+    2.0, and a batch of 1024 systems with n_i log-uniform in [2^10, 2^18]
+    (ratio 1.01), each beside the double-float and (at 1.01) the plain fp64
+    solve, with iterations, status and the error against the fp64 oracle
+    (rank 0 of a one-GPU run) or the manufactured solution."""
+    import torch
+
+    with_oracle = rank == 0 and world == 1 and not a.no_cpu
+    if with_oracle:
+        import oracle
+
+    def run(plan, solve, x, steps=3):
+        solve()
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            solve()
+        e1.record(stream)
+        stream.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1) / steps, world), plan.query()
+
+    out = {}
+    n = a.n
+    for ratio in (1.01, 1.1, 2.0):
+        g = synth.system_device(1005 + rank, n, kind=synth.KIND_RATIO, ratio=ratio)
+        x = torch.empty_like(g["b"])
+        ref = host = None
+        if with_oracle:
+            host = {k: g[k].cpu().numpy() for k in "abcd"}
+            ref = oracle.thomas(host["a"], host["b"], host["c"], host["d"])
+        row = {"n": n, "ratio": ratio}
+        for dt in (("mixed", "f64_df", "f64") if ratio == 1.01 else ("mixed", "f64_df")):
+            plan = binding.Plan(n, dtype=dt, flags=binding.TUNE_PREDICT)
+            ms, q = run(plan, lambda: plan.solve(g["a"], g["b"], g["c"], g["d"], x,
+                                                 stream=stream), x)
+            r = {"value": world * n / (ms * 1e-3), "ms_per_step": ms,
+                 "iterations": q["iterations"], "status": q["status_name"],
+                 "rel_fwd_vs_x_true": ((x - g["x_true"]).abs().max()
+                                       / g["x_true"].abs().max()).item()}
+            if with_oracle:
+                xh = x.cpu().numpy()
+                r["rel_fwd_vs_oracle"] = oracle.rel_forward_error(xh, ref)
+                r["rel_residual_host"] = oracle.rel_residual(host["a"], host["b"], host["c"],
+                                                             host["d"], xh)
+            row[dt] = r
+            del plan
+        out[f"ratio_{ratio}"] = row
+        del g, x, host, ref
+    sizes = synth.batch_sizes(1007 + rank, 1024, 10, 18)
+    off = synth.offsets_from_sizes(sizes)
+    nb = int(off[-1])
+    g = synth.system_device(1007 + rank, nb, kind=synth.KIND_RATIO, ratio=1.01, offsets=off)
+    offs = torch.as_tensor(off, device="cuda")
+    x = torch.empty_like(g["b"])
+    ref = host = None
+    if with_oracle:
+        host = {k: g[k].cpu().numpy() for k in "abcd"}
+        ref = oracle.thomas_batched(off, host["a"], host["b"], host["c"], host["d"])
+    row = {"systems": 1024, "rows": nb, "ratio": 1.01}
+    for dt in ("mixed", "f64_df", "f64"):
+        plan = binding.Plan(nb, dtype=dt, batch_max=1024, flags=binding.TUNE_PREDICT)
+        ms, q = run(plan, lambda: plan.solve_batched(offs, g["a"], g["b"], g["c"], g["d"], x,
+                                                     host_offsets=off, stream=stream), x)
+        r = {"value": world * nb / (ms * 1e-3), "ms_per_step": ms,
+             "iterations": q["iterations"], "status": q["status_name"],
+             "rel_fwd_vs_x_true": ((x - g["x_true"]).abs().max()
+                                   / g["x_true"].abs().max()).item()}
+        if with_oracle:
+            xh = x.cpu().numpy()
+            r["rel_fwd_vs_oracle"] = oracle.rel_forward_error(xh, ref)
+            r["rel_residual_host"] = float(
+                np.max(np.abs(oracle.residual_batched(off, host["a"], host["b"], host["c"],
+                                                      host["d"], xh)))
+                / np.max(np.abs(host["d"])))
+        row[dt] = r
+        del plan
+    out["batch_1024"] = row
+    return out
 
 
 def extra_workloads(binding, synth, world, rank, stream, a):
@@ -412,30 +530,7 @@ def extra_workloads(binding, synth, world, rank, stream, a):
         del arrs, x, plan
     out["batched"] = res
     del gb, offs
-    n = a.n
-    g = synth.system_device(1005 + rank, n, kind=synth.KIND_RATIO, ratio=1.01)
-    x = torch.empty_like(g["b"])
-    mres = {"n": n, "ratio": 1.01}
-    for dt in ("mixed", "f64_df", "f64"):
-        plan = binding.Plan(n, dtype=dt, flags=binding.TUNE_PREDICT)
-        plan.solve(g["a"], g["b"], g["c"], g["d"], x, stream=stream)
-        stream.synchronize()
-        steps = 3
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            plan.solve(g["a"], g["b"], g["c"], g["d"], x, stream=stream)
-        e1.record(stream)
-        stream.synchronize()
-        ms = max_over_ranks(e0.elapsed_time(e1) / steps, world)
-        q = plan.query()
-        err = ((x - g["x_true"]).abs().max() / g["x_true"].abs().max()).item()
-        mres[dt] = {"value": world * n / (ms * 1e-3), "ms_per_step": ms,
-                    "iterations": q["iterations"], "status": q["status_name"],
-                    "rel_fwd_vs_x_true": err}
-        del plan
-    out["mixed"] = mres
-    del g, x
+    out["mixed"] = mixed_workloads(binding, synth, world, rank, stream, a)
     # mid-size single systems: the single-launch on-chip solve against the
     # level-by-level route (inputs fit in L2, so these are L2-warm times)
     mid = {}
@@ -511,6 +606,9 @@ def main():
     x = torch.empty_like(g["b"])
     torch.cuda.synchronize()
     hbm_peak, peak_kind = peaks()
+    # this GPU's fp64 pipe: thread fma / mul / add instructions per second
+    fp64_rates = binding.measure_fp64_rates()
+    fp64_peak = max(fp64_rates)
     out = {}
     with Clocks(dev) as clk:
         # tuned: double-float arithmetic; block size from the predictor, then
@@ -525,12 +623,23 @@ def main():
             m_tuned, _ = plan.autotune(g["a"], g["b"], g["c"], g["d"], x, reps=3, stream=stream)
         ms, info = time_device(plan, g, x, a.steps, a.warmup, world, stream)
         err_true, res = verify(g, x)
+        # the predictor's live regret: its block size timed on the same
+        # arrays, against the exhaustive search's choice
+        if m_pred != m_tuned:
+            plan_pr = binding.Plan(n, dtype="f64_df", m=m_pred, m_reduced=a.m_reduced,
+                                   flags=binding.TRACE | binding.GRAPH)
+            xr = torch.empty_like(x)
+            ms_pred, _ = time_device(plan_pr, g, xr, max(5, a.steps // 2), 2, world, stream)
+            del plan_pr, xr
+        else:
+            ms_pred = ms
         # plain: native fp64 arithmetic
         xp = torch.empty_like(x)
         plan_p = binding.Plan(n, dtype="f64", m=a.m, m_reduced=a.m_reduced, flags=binding.TRACE)
         msp, infop = time_device(plan_p, g, xp, max(3, a.steps // 4), min(a.warmup, 3), world,
                                  stream)
         err_true_p, res_p = verify(g, xp)
+        xp_host = xp.cpu() if (rank == 0 and world == 1 and not a.no_cpu) else None
         del xp
         # end to end from pinned host buffers
         hk = {k: g[k].cpu().pin_memory() for k in "abcd"}
@@ -571,6 +680,12 @@ def main():
             / g["x_true"].abs().max().item()
         # one system per call (tps_solve_host_async): no overlap between steps
         _, single_ms = time_host(plan_h, hk, hx, stream, esteps, min(a.warmup, 3), world)
+        # the predictor's (S, chunk) without the search, the same single calls
+        plan_hp = binding.Plan(n, dtype="f64_df", residency="host", m=infoh["m"],
+                               m_reduced=a.m_reduced, streams=pred_h["streams"],
+                               chunk=pred_h["chunk"])
+        _, single_ms_pred = time_host(plan_hp, hk, hx, stream, esteps, min(a.warmup, 3), world)
+        del plan_hp
         floor_ms, h2d_ms = link_floor(hk, hx, g, x, stream)
         del plan_h
         # zero copy: kernels on host memory, pinned and pageable
@@ -598,6 +713,22 @@ def main():
 
     value = job_value(n, world, ms)
     s1, s2, s3, tot = info["stage_ms"]
+    # plain (native fp64) roofline: fp64-pipe instructions of its Stage 1
+    # (the committed ncu count per row) over its event time, against this
+    # GPU's measured fp64 FMA rate
+    s1p = infop["stage_ms"][0]
+    f64t = fp64_table().get(f"k_stage1_f64_m{infop['m']}")
+    plain_roof = {"bound": "fp64", "kernel": "k_stage1", "peak": fp64_peak / 1e9,
+                  "unit": "G fp64-pipe thread-inst/s",
+                  "peak_kind": "measured: the fastest of fp64 fma / mul / add chains "
+                               "(tps_measure_fp64_rates)",
+                  "peak_rates": {"fma": fp64_rates[0] / 1e9, "mul": fp64_rates[1] / 1e9,
+                                 "add": fp64_rates[2] / 1e9},
+                  "inst_per_row": f64t, "kernel_source": kernel_source_hash(),
+                  "achieved": (f64t * n / (s1p * 1e-3) / 1e9) if f64t else None}
+    plain_roof["frac"] = (plain_roof["achieved"] / plain_roof["peak"]
+                          if plain_roof["achieved"] else None)
+    plain_roof["frac_step_hbm"] = 40 * n / (msp * 1e-3) / 1e9 / hbm_peak
     dominant = "k_stage1" if s1 >= s3 else "k_stage3"
     dom_ms = max(s1, s3)
     alg_bytes = (32 if dominant == "k_stage1" else 40) * n
@@ -621,13 +752,27 @@ def main():
         "err": {"rel_fwd_vs_x_true": err_true, "rel_residual": res},
         "stage_ms": {"stage1": s1, "stage2": s2, "stage3": s3, "total": tot},
         "plain": {"value": world * n / (msp * 1e-3), "ms_per_step": msp, "dtype": "f64",
-                  "stage_ms": infop["stage_ms"],
+                  "stage_ms": infop["stage_ms"], "m": infop["m"], "roofline": plain_roof,
                   "err": {"rel_fwd_vs_x_true": err_true_p, "rel_residual": res_p}},
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": hbm_peak,
                      "unit": "GB/s", "frac": achieved / hbm_peak,
                      "traffic": (traffic * n if traffic else None),
                      "peak_kind": peak_kind,
-                     "alg_bytes_per_row": alg_bytes // n, "kernel_source": kernel_hash},
+                     "alg_bytes_per_row": alg_bytes // n, "kernel_source": kernel_hash,
+                     "frac_step": 40 * n / (ms * 1e-3) / 1e9 / hbm_peak,
+                     "frac_step_note": "the whole solve: 40 B/row (a, b, c, d read, x "
+                                       "written) over ms_per_step, of measured HBM"},
+        "predictor": {"m_predicted": m_pred, "m_autotuned": m_tuned,
+                      "ms_predicted": ms_pred, "ms_autotuned": ms,
+                      "regret_live": ms_pred / ms - 1.0,
+                      "host": {"predicted": {"streams": pred_h["streams"], "chunk": pred_h["chunk"],
+                                             "ms": single_ms_pred},
+                               "autotuned": {"streams": infoh["streams"], "chunk": infoh["chunk"],
+                                             "ms": single_ms},
+                               "regret_live": single_ms_pred / single_ms - 1.0},
+                      "note": "T(prediction) / T(exhaustive search's choice) - 1, both timed "
+                              "here on the same arrays (negative: the search's pick measured "
+                              "slower in its own timing run)"},
         "e2e": {"value": world * n / (ems * 1e-3), "unit": UNIT, "ms_per_step": ems,
                 "steps": esteps, "h2d_bytes_per_step": 4 * 8 * n, "d2h_bytes_per_step": 8 * n,
                 "streams": infoh["streams"], "chunk": infoh["chunk"],
@@ -643,13 +788,30 @@ def main():
         "clocks": clocks,
     }
     line.update(extra)
+    checks = [("value", err_true, res), ("plain", err_true_p, res_p)]
     if rank == 0 and world == 1 and not a.no_cpu:
-        cpu, err_o, res_o, _ = cpu_oracle_leg(g, x)
+        import oracle
+
+        cpu, err_o, res_o, ref = cpu_oracle_leg(g, x)
         line["cpu_baseline"] = cpu
         line["err"]["rel_fwd_vs_oracle"] = err_o
         line["err"]["rel_residual_host"] = res_o
+        xph = xp_host.numpy()
+        err_op = oracle.rel_forward_error(xph, ref)
+        res_op = oracle.rel_residual(*(g[k].cpu().numpy() for k in "abcd"), xph)
+        line["plain"]["err"]["rel_fwd_vs_oracle"] = err_op
+        line["plain"]["err"]["rel_residual_host"] = res_op
+        checks = [("value", err_o, res_o), ("plain", err_op, res_op)]
+    # the accuracy gate: every reported solve meets the fp64 bar (against
+    # the oracle when it ran, else against the manufactured solution)
+    failed = [nm for nm, e, r in checks if not (e <= GATE_FWD and r <= GATE_RES)]
+    line["gate"] = {"rel_fwd_max": GATE_FWD, "rel_residual_max": GATE_RES,
+                    "against": "oracle" if "cpu_baseline" in line else "x_true",
+                    "passed": not failed, "failed": failed}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if failed:
+        sys.exit(1)
     if world > 1:
         import torch.distributed as dist
 

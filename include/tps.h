@@ -403,6 +403,16 @@ int32_t tps_paper_predict_streams(double size, const double* sum_model, const do
  * is not finite. */
 tps_status tps_plan_query(tps_plan_t plan, tps_info* out);
 
+/* Measurement aid (the paper has no counterpart): the current device's
+ * fp64 instruction rates -- fused multiply-add, multiply and add, in
+ * thread instructions per second (any pointer may be NULL) -- from
+ * synthetic kernels of independent dependency chains on every SM (for each
+ * kind the best of ten launches of a few ms at two occupancies, on the
+ * legacy default stream; allocates and frees a small buffer and
+ * synchronises the device).  They are the peaks against which the plain
+ * fp64 solve, bound by the fp64 pipe on GB300, is reported. */
+tps_status tps_measure_fp64_rates(double* fma_per_s, double* mul_per_s, double* add_per_s);
+
 /* Static description of a status code. */
 const char* tps_status_string(tps_status s);
 

@@ -7,8 +7,10 @@ and the two share no code.
 
 Contents
   * ``liboracle.so`` (``oracle.c``): serial fp64 Thomas, a serial partition
-    solver that follows the method's three stages (Sec. 1, Sec. 2.2), dense
-    Gaussian elimination with partial pivoting, residuals and norms.
+    solver that follows the method's three stages (Sec. 1, Sec. 2.2), the
+    same with Stages 1 and 3 over host threads (the multi-core CPU
+    baseline), dense Gaussian elimination with partial pivoting, residuals
+    and norms.
   * ``heuristic.py``: the paper's stream-count time models (Eq. 1-7) and the
     optimum-stream rule (Eq. 6), in plain Python.
   * ``mlp.py``: the launch-parameter MLP forward/backward in fp64 numpy.
@@ -39,7 +41,7 @@ def build(force: bool = False) -> str:
     """Compile ``oracle.c`` into ``liboracle.so`` next to it (plain gcc)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", "-o", _LIB + ".tmp", _SRC, "-lm"]
+               "-pthread", "-shared", "-o", _LIB + ".tmp", _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(_LIB + ".tmp", _LIB)
     return _LIB
@@ -56,6 +58,7 @@ def _load():
         lib.orc_thomas_batched.argtypes = [I, P, P, P, P, P, P]
         lib.orc_partition.argtypes = [I, I, P, P, P, P, P]
         lib.orc_partition_ex.argtypes = [I, I, P, P, P, P, P, P, P, P, P]
+        lib.orc_partition_threaded.argtypes = [I, I, P, P, P, P, P, ctypes.c_int]
         lib.orc_partition_reduced_size.argtypes = [I, I]
         lib.orc_partition_reduced_size.restype = I
         lib.orc_dense_ge.argtypes = [I, P, P, P, P, P]
@@ -65,7 +68,7 @@ def _load():
         lib.orc_maxabs_diff.argtypes = [I, P, P, P, P]
         lib.orc_maxabs_diff.restype = None
         for f in ("orc_thomas", "orc_thomas_batched", "orc_partition", "orc_partition_ex",
-                  "orc_dense_ge", "orc_thomas_f32"):
+                  "orc_partition_threaded", "orc_dense_ge", "orc_thomas_f32"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -134,6 +137,19 @@ def partition(a, b, c, d, m, return_reduced=False):
     _check(lib.orc_partition_ex(n, int(m), _p(a), _p(b), _p(c), _p(d), _p(x),
                                 *[_p(r) for r in red]), "partition")
     return x, tuple(r[:nr] for r in red)
+
+
+def partition_threaded(a, b, c, d, m, threads=None):
+    """The partition solve with Stages 1 and 3 over ``threads`` host threads
+    (default: every core of the host), Stage 2 serial: the multi-core CPU
+    baseline.  Bit-identical to :func:`partition`."""
+    a, b, c, d = map(_f64, (a, b, c, d))
+    n = b.shape[0]
+    t = int(threads or os.cpu_count() or 1)
+    x = np.empty(n, dtype=np.float64)
+    _check(_load().orc_partition_threaded(n, int(m), _p(a), _p(b), _p(c), _p(d), _p(x), t),
+           "partition_threaded")
+    return x
 
 
 def reduced_size(n, m):

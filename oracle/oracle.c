@@ -30,6 +30,7 @@
  *   returns A^{-1} d up to rounding, which is how the tests pin it.
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -134,115 +135,215 @@ int64_t orc_partition_reduced_size(int64_t n, int64_t m) {
   return 2 * p - (last == 1 ? 1 : 0);
 }
 
+/* Stage 1 of block k (rows r0 .. r1, L = r1 - r0 + 1): y, v, w of its
+ * interior rows and its reduced rows 2k, 2k+1.  gam: m doubles of scratch.
+ * Blocks touch disjoint parts of y, v, w and the reduced arrays. */
+static int stage1_block(int64_t k, int64_t p, int64_t n, int64_t m, const double *a,
+                        const double *b, const double *c, const double *d, double *y,
+                        double *v, double *w, double *ra, double *rb, double *rc, double *rd,
+                        double *gam) {
+  const int64_t r0 = k * m;
+  const int64_t r1 = (r0 + m < n ? r0 + m : n) - 1;
+  const int64_t L = r1 - r0 + 1;
+  const int64_t jf = 2 * k;      /* reduced index of f_k */
+  const int64_t jl = 2 * k + 1;  /* reduced index of l_k (if L >= 2) */
+  if (L >= 3) {
+    /* Thomas on T with the three right-hand sides d_int, a[r0+1] e_1,
+     * c[r1-1] e_last, column by column, sharing the pivots. */
+    const int64_t i0 = r0 + 1, ie = r1 - 1, ni = ie - i0 + 1;
+    double beta = b[i0];
+    if (beta == 0.0 || !isfinite(beta)) return ORC_ZERO_PIVOT;
+    y[i0] = d[i0] / beta;
+    v[i0] = a[i0] / beta;
+    w[i0] = (ni == 1 ? c[ie] : 0.0) / beta;
+    for (int64_t t = 1; t < ni; ++t) {
+      const int64_t i = i0 + t;
+      gam[t - 1] = c[i - 1] / beta;
+      beta = b[i] - a[i] * gam[t - 1];
+      if (beta == 0.0 || !isfinite(beta)) return ORC_ZERO_PIVOT;
+      const double rhs_w = (i == ie) ? c[ie] : 0.0;
+      y[i] = (d[i] - a[i] * y[i - 1]) / beta;
+      v[i] = (0.0 - a[i] * v[i - 1]) / beta;
+      w[i] = (rhs_w - a[i] * w[i - 1]) / beta;
+    }
+    for (int64_t t = ni - 2; t >= 0; --t) {
+      const int64_t i = i0 + t;
+      y[i] = y[i] - gam[t] * y[i + 1];
+      v[i] = v[i] - gam[t] * v[i + 1];
+      w[i] = w[i] - gam[t] * w[i + 1];
+    }
+    /* first reduced row (unknowns l_{k-1}, f_k, l_k) */
+    ra[jf] = (k > 0) ? a[r0] : 0.0;
+    rb[jf] = b[r0] - c[r0] * v[i0];
+    rc[jf] = 0.0 - c[r0] * w[i0];
+    rd[jf] = d[r0] - c[r0] * y[i0];
+    /* last reduced row (unknowns f_k, l_k, f_{k+1}) */
+    ra[jl] = 0.0 - a[r1] * v[ie];
+    rb[jl] = b[r1] - a[r1] * w[ie];
+    rc[jl] = (k < p - 1) ? c[r1] : 0.0;
+    rd[jl] = d[r1] - a[r1] * y[ie];
+  } else if (L == 2) {
+    ra[jf] = (k > 0) ? a[r0] : 0.0;
+    rb[jf] = b[r0];
+    rc[jf] = c[r0];
+    rd[jf] = d[r0];
+    ra[jl] = a[r1];
+    rb[jl] = b[r1];
+    rc[jl] = (k < p - 1) ? c[r1] : 0.0;
+    rd[jl] = d[r1];
+  } else { /* L == 1: only the last block can be this short */
+    ra[jf] = (k > 0) ? a[r0] : 0.0;
+    rb[jf] = b[r0];
+    rc[jf] = 0.0;
+    rd[jf] = d[r0];
+  }
+  return ORC_OK;
+}
+
+/* Stage 3 of block k: x_int = y - v f_k - w l_k from the reduced solution. */
+static void stage3_block(int64_t k, int64_t n, int64_t m, const double *y, const double *v,
+                         const double *w, const double *rx, double *x) {
+  const int64_t r0 = k * m;
+  const int64_t r1 = (r0 + m < n ? r0 + m : n) - 1;
+  const int64_t L = r1 - r0 + 1;
+  const double f = rx[2 * k];
+  const double l = (L >= 2) ? rx[2 * k + 1] : f;
+  x[r0] = f;
+  x[r1] = l;
+  for (int64_t i = r0 + 1; i <= r1 - 1; ++i) x[i] = y[i] - v[i] * f - w[i] * l;
+}
+
+/* The work arrays of one partition solve. */
+typedef struct {
+  int64_t n, m, p, nr;
+  const double *a, *b, *c, *d;
+  double *x, *y, *v, *w, *ra, *rb, *rc, *rd, *rx;
+} part_ctx;
+
+static int part_alloc(part_ctx *P, int64_t n, int64_t m, const double *a, const double *b,
+                      const double *c, const double *d, double *x) {
+  memset(P, 0, sizeof(*P));
+  P->n = n; P->m = m; P->p = (n + m - 1) / m;
+  P->nr = orc_partition_reduced_size(n, m);
+  P->a = a; P->b = b; P->c = c; P->d = d; P->x = x;
+  P->y = (double *)calloc((size_t)n, sizeof(double));
+  P->v = (double *)calloc((size_t)n, sizeof(double));
+  P->w = (double *)calloc((size_t)n, sizeof(double));
+  P->ra = (double *)calloc((size_t)P->nr, sizeof(double));
+  P->rb = (double *)calloc((size_t)P->nr, sizeof(double));
+  P->rc = (double *)calloc((size_t)P->nr, sizeof(double));
+  P->rd = (double *)calloc((size_t)P->nr, sizeof(double));
+  P->rx = (double *)calloc((size_t)P->nr, sizeof(double));
+  return (P->y && P->v && P->w && P->ra && P->rb && P->rc && P->rd && P->rx) ? ORC_OK
+                                                                              : ORC_NO_MEMORY;
+}
+
+static void part_free(part_ctx *P) {
+  free(P->y); free(P->v); free(P->w);
+  free(P->ra); free(P->rb); free(P->rc); free(P->rd); free(P->rx);
+}
+
 int orc_partition_ex(int64_t n, int64_t m, const double *a, const double *b, const double *c,
                      const double *d, double *x, double *red_a, double *red_b, double *red_c,
                      double *red_d) {
   if (n < 0 || m < 2) return ORC_BAD_ARG;
   if (n == 0) return ORC_OK;
-  const int64_t p = (n + m - 1) / m;
-  const int64_t nr = orc_partition_reduced_size(n, m);
-
-  /* y, v, w for every interior row (kept at the row's own index). */
-  double *y = (double *)calloc((size_t)n, sizeof(double));
-  double *v = (double *)calloc((size_t)n, sizeof(double));
-  double *w = (double *)calloc((size_t)n, sizeof(double));
-  double *ra = (double *)calloc((size_t)nr, sizeof(double));
-  double *rb = (double *)calloc((size_t)nr, sizeof(double));
-  double *rc = (double *)calloc((size_t)nr, sizeof(double));
-  double *rd = (double *)calloc((size_t)nr, sizeof(double));
-  double *rx = (double *)calloc((size_t)nr, sizeof(double));
-  double *gam = (double *)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
-  int st = ORC_OK;
-  if (!y || !v || !w || !ra || !rb || !rc || !rd || !rx || !gam) {
+  part_ctx P;
+  int st = part_alloc(&P, n, m, a, b, c, d, x);
+  double *gam = (double *)malloc((size_t)m * sizeof(double));
+  if (st != ORC_OK || !gam) {
     st = ORC_NO_MEMORY;
     goto done;
   }
-
   /* ---- Stage 1 ---- */
-  for (int64_t k = 0; k < p && st == ORC_OK; ++k) {
-    const int64_t r0 = k * m;
-    const int64_t r1 = (r0 + m < n ? r0 + m : n) - 1;
-    const int64_t L = r1 - r0 + 1;
-    const int64_t jf = 2 * k;      /* reduced index of f_k */
-    const int64_t jl = 2 * k + 1;  /* reduced index of l_k (if L >= 2) */
-    if (L >= 3) {
-      /* Thomas on T with the three right-hand sides d_int, a[r0+1] e_1,
-       * c[r1-1] e_last, column by column, sharing the pivots. */
-      const int64_t i0 = r0 + 1, ie = r1 - 1, ni = ie - i0 + 1;
-      double beta = b[i0];
-      if (beta == 0.0 || !isfinite(beta)) { st = ORC_ZERO_PIVOT; break; }
-      y[i0] = d[i0] / beta;
-      v[i0] = a[i0] / beta;
-      w[i0] = (ni == 1 ? c[ie] : 0.0) / beta;
-      for (int64_t t = 1; t < ni; ++t) {
-        const int64_t i = i0 + t;
-        gam[t - 1] = c[i - 1] / beta;
-        beta = b[i] - a[i] * gam[t - 1];
-        if (beta == 0.0 || !isfinite(beta)) { st = ORC_ZERO_PIVOT; break; }
-        const double rhs_w = (i == ie) ? c[ie] : 0.0;
-        y[i] = (d[i] - a[i] * y[i - 1]) / beta;
-        v[i] = (0.0 - a[i] * v[i - 1]) / beta;
-        w[i] = (rhs_w - a[i] * w[i - 1]) / beta;
-      }
-      if (st != ORC_OK) break;
-      for (int64_t t = ni - 2; t >= 0; --t) {
-        const int64_t i = i0 + t;
-        y[i] = y[i] - gam[t] * y[i + 1];
-        v[i] = v[i] - gam[t] * v[i + 1];
-        w[i] = w[i] - gam[t] * w[i + 1];
-      }
-      /* first reduced row (unknowns l_{k-1}, f_k, l_k) */
-      ra[jf] = (k > 0) ? a[r0] : 0.0;
-      rb[jf] = b[r0] - c[r0] * v[i0];
-      rc[jf] = 0.0 - c[r0] * w[i0];
-      rd[jf] = d[r0] - c[r0] * y[i0];
-      /* last reduced row (unknowns f_k, l_k, f_{k+1}) */
-      ra[jl] = 0.0 - a[r1] * v[ie];
-      rb[jl] = b[r1] - a[r1] * w[ie];
-      rc[jl] = (k < p - 1) ? c[r1] : 0.0;
-      rd[jl] = d[r1] - a[r1] * y[ie];
-    } else if (L == 2) {
-      ra[jf] = (k > 0) ? a[r0] : 0.0;
-      rb[jf] = b[r0];
-      rc[jf] = c[r0];
-      rd[jf] = d[r0];
-      ra[jl] = a[r1];
-      rb[jl] = b[r1];
-      rc[jl] = (k < p - 1) ? c[r1] : 0.0;
-      rd[jl] = d[r1];
-    } else { /* L == 1: only the last block can be this short */
-      ra[jf] = (k > 0) ? a[r0] : 0.0;
-      rb[jf] = b[r0];
-      rc[jf] = 0.0;
-      rd[jf] = d[r0];
+  for (int64_t k = 0; k < P.p && st == ORC_OK; ++k)
+    st = stage1_block(k, P.p, n, m, a, b, c, d, P.y, P.v, P.w, P.ra, P.rb, P.rc, P.rd, gam);
+  if (st != ORC_OK) goto done;
+  /* ---- Stage 2: reduced system by Thomas ---- */
+  st = orc_thomas(P.nr, P.ra, P.rb, P.rc, P.rd, P.rx);
+  if (st != ORC_OK) goto done;
+  /* ---- Stage 3 ---- */
+  for (int64_t k = 0; k < P.p; ++k) stage3_block(k, n, m, P.y, P.v, P.w, P.rx, x);
+  if (red_a) memcpy(red_a, P.ra, (size_t)P.nr * sizeof(double));
+  if (red_b) memcpy(red_b, P.rb, (size_t)P.nr * sizeof(double));
+  if (red_c) memcpy(red_c, P.rc, (size_t)P.nr * sizeof(double));
+  if (red_d) memcpy(red_d, P.rd, (size_t)P.nr * sizeof(double));
+done:
+  part_free(&P);
+  free(gam);
+  return st;
+}
+
+/* ------------------------------------------------------------------------
+ * The same partition solve with Stages 1 and 3 spread over `threads` host
+ * threads (each a contiguous run of blocks; Stage 2 stays serial): the
+ * multi-core CPU baseline.  Per block the arithmetic is that of
+ * orc_partition_ex, in the same order, so the result is bit-identical.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  part_ctx *P;
+  int64_t k0, k1;
+  int stage, status;
+} part_job;
+
+static void *part_worker(void *arg) {
+  part_job *J = (part_job *)arg;
+  part_ctx *P = J->P;
+  J->status = ORC_OK;
+  if (J->stage == 1) {
+    double *gam = (double *)malloc((size_t)P->m * sizeof(double));
+    if (!gam) { J->status = ORC_NO_MEMORY; return NULL; }
+    for (int64_t k = J->k0; k < J->k1 && J->status == ORC_OK; ++k)
+      J->status = stage1_block(k, P->p, P->n, P->m, P->a, P->b, P->c, P->d, P->y, P->v, P->w,
+                               P->ra, P->rb, P->rc, P->rd, gam);
+    free(gam);
+  } else {
+    for (int64_t k = J->k0; k < J->k1; ++k)
+      stage3_block(k, P->n, P->m, P->y, P->v, P->w, P->rx, P->x);
+  }
+  return NULL;
+}
+
+static int part_parallel(part_ctx *P, int stage, int threads) {
+  pthread_t tid[256];
+  part_job job[256];
+  if (threads > 256) threads = 256;
+  if (threads < 1) threads = 1;
+  int started = 0, st = ORC_OK;
+  for (int t = 0; t < threads; ++t) {
+    job[t].P = P;
+    job[t].stage = stage;
+    job[t].k0 = P->p * t / threads;
+    job[t].k1 = P->p * (t + 1) / threads;
+    job[t].status = ORC_OK;
+    if (pthread_create(&tid[t], NULL, part_worker, &job[t]) != 0) {
+      part_worker(&job[t]);  /* run it on this thread instead */
+      if (job[t].status != ORC_OK) st = job[t].status;
+      tid[t] = 0;
+      continue;
+    }
+    ++started;
+  }
+  for (int t = 0; t < threads; ++t) {
+    if (tid[t]) {
+      pthread_join(tid[t], NULL);
+      if (job[t].status != ORC_OK) st = job[t].status;
     }
   }
-  if (st != ORC_OK) goto done;
+  (void)started;
+  return st;
+}
 
-  /* ---- Stage 2: reduced system by Thomas ---- */
-  st = orc_thomas(nr, ra, rb, rc, rd, rx);
-  if (st != ORC_OK) goto done;
-
-  /* ---- Stage 3 ---- */
-  for (int64_t k = 0; k < p; ++k) {
-    const int64_t r0 = k * m;
-    const int64_t r1 = (r0 + m < n ? r0 + m : n) - 1;
-    const int64_t L = r1 - r0 + 1;
-    const double f = rx[2 * k];
-    const double l = (L >= 2) ? rx[2 * k + 1] : f;
-    x[r0] = f;
-    x[r1] = l;
-    for (int64_t i = r0 + 1; i <= r1 - 1; ++i) x[i] = y[i] - v[i] * f - w[i] * l;
-  }
-  if (red_a) memcpy(red_a, ra, (size_t)nr * sizeof(double));
-  if (red_b) memcpy(red_b, rb, (size_t)nr * sizeof(double));
-  if (red_c) memcpy(red_c, rc, (size_t)nr * sizeof(double));
-  if (red_d) memcpy(red_d, rd, (size_t)nr * sizeof(double));
-
-done:
-  free(y); free(v); free(w);
-  free(ra); free(rb); free(rc); free(rd); free(rx);
-  free(gam);
+int orc_partition_threaded(int64_t n, int64_t m, const double *a, const double *b,
+                           const double *c, const double *d, double *x, int threads) {
+  if (n < 0 || m < 2 || threads < 1) return ORC_BAD_ARG;
+  if (n == 0) return ORC_OK;
+  part_ctx P;
+  int st = part_alloc(&P, n, m, a, b, c, d, x);
+  if (st == ORC_OK) st = part_parallel(&P, 1, threads);
+  if (st == ORC_OK) st = orc_thomas(P.nr, P.ra, P.rb, P.rc, P.rd, P.rx);
+  if (st == ORC_OK) st = part_parallel(&P, 3, threads);
+  part_free(&P);
   return st;
 }
 

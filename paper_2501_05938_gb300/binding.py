@@ -26,7 +26,7 @@ HOST_OVERLAP = 256
 # every symbol include/tps.h declares
 EXPORTS = ("tps_plan", "tps_plan_destroy", "tps_workspace_size", "tps_set_workspace", "tps_solve",
            "tps_solve_batched", "tps_solve_host_async", "tps_solve_host_many_async",
-           "tps_plan_query", "tps_status_string", "tps_version")
+           "tps_plan_query", "tps_status_string", "tps_version", "tps_measure_fp64_rates")
 
 
 class PlanDesc(ctypes.Structure):
@@ -237,6 +237,19 @@ class Plan:
                 "last_correction": info.last_correction,
                 "stage_ms": list(info.stage_ms), "workspace_bytes": info.workspace_bytes,
                 "pageable_ok": bool(info.pageable_ok), "onchip": info.onchip}
+
+
+def measure_fp64_rates():
+    """tps_measure_fp64_rates: fp64 (fma, mul, add) thread instructions per
+    second of the current device (synchronises it)."""
+    L = lib()
+    f = L.tps_measure_fp64_rates
+    D = ctypes.POINTER(ctypes.c_double)
+    f.argtypes = [D, D, D]
+    f.restype = ctypes.c_int
+    v = [ctypes.c_double() for _ in range(3)]
+    check(f(*(ctypes.byref(t) for t in v)), "tps_measure_fp64_rates")
+    return tuple(t.value for t in v)
 
 
 def status_string(s):

@@ -223,3 +223,15 @@ def test_thomas_f32_is_single_precision():
     assert x32.dtype == np.float32
     err = oracle.rel_forward_error(x32.astype(np.float64), x64)
     assert 1e-9 < err < 6 * 64 * np.finfo(np.float32).eps
+
+
+@pytest.mark.parametrize("n,m,threads", [(1000, 7, 3), (100003, 128, 8), (65, 64, 4),
+                                         (2, 2, 16), (1, 5, 2), (4097, 32, 1)])
+def test_threaded_partition_is_the_serial_partition(n, m, threads):
+    """The multi-core CPU baseline runs the serial oracle's per-block
+    arithmetic in the same order, so its x is the same bits (and is pinned
+    through the serial partition's own pins)."""
+    s = synth.system(90 + n, n)
+    x1 = oracle.partition(s["a"], s["b"], s["c"], s["d"], m)
+    x2 = oracle.partition_threaded(s["a"], s["b"], s["c"], s["d"], m, threads=threads)
+    np.testing.assert_array_equal(x2, x1)
