@@ -196,16 +196,20 @@ tps_status tps_set_workspace(tps_plan_t plan, void* dev_ptr, size_t bytes);
  *
  * TPS_TRUNCATE (device plans, fp64 / double-float / fp32; not the paper's
  * method, an approximation for strongly dominant systems): windows of m kept
- * rows are solved independently, each on chip as the system on the window
- * plus m_reduced halo rows on either side with the couplings beyond cut; one
- * pass over the arrays, no reduced system.  m (even) and m_reduced (even)
- * must satisfy m + 2 m_reduced <= 1792; 0 chooses (the halo for the plan's
- * tol at a dominance factor max(|a|+|c|)/|b| of 3/4, the window from the
- * rest).  Each window bounds its own error from its dominance factor q and
- * smallest |b|: (|a_cut| q^h + |c_cut| q^h) / ((1 - q) min|b|) relative to
- * max|x|; tps_plan_query reports the largest bound of the last solve in
- * last_correction and TPS_ERR_NO_CONVERGENCE if it exceeds tol (default
- * 1e-12).
+ * rows are solved independently, each as the system on the window plus
+ * m_reduced halo rows on either side with the couplings beyond cut; one
+ * pass over the arrays, no reduced system across windows.  m (even) and
+ * m_reduced (even) must satisfy m + 2 m_reduced <= 1792 (one CTA per
+ * window, on chip) or m + 2 m_reduced = 32 mb with 8 <= mb <= 256 (one warp
+ * per window: 32 blocks of mb rows, one per lane, the partition method
+ * inside the warp, the blocks' row relations kept in a workspace buffer of
+ * about 24 bytes per row that stays mostly in L2); 0 chooses (the halo for
+ * the plan's tol at a dominance factor max(|a|+|c|)/|b| of 3/4, one-warp
+ * windows of 32 blocks of 256 rows).  Each window bounds its own error from
+ * its dominance factor q and smallest |b|: (|a_cut| q^h + |c_cut| q^h) /
+ * ((1 - q) min|b|) relative to max|x|; tps_plan_query reports the largest
+ * bound of the last solve in last_correction and TPS_ERR_NO_CONVERGENCE if
+ * it exceeds tol (default 1e-12).
  * The barrier waits a bounded time; if it runs out (which needs CTAs that
  * are not co-resident) the solve stops and tps_plan_query reports
  * TPS_ERR_TIMEOUT. */

@@ -247,9 +247,9 @@ __device__ __forceinline__ void PieceMap<Tin, R>::init(const Level& lv, int64_t 
 // length) of src[0..n_arr) into the buffer's arrays.  kVec16: whole pieces
 // go as one 16-byte copy (arrays 16-byte aligned, m a multiple of kVec);
 // otherwise, and for a block's ragged last piece, element by element.
-template <class Tin, int R, bool kVec16>
+template <class Tin, int R, bool kVec16, class PM>
 __device__ __forceinline__ void load_chunk(Tin* buf, const Tin* const* src, int n_arr,
-                                           const PieceMap<Tin, R>& pm, int row0) {
+                                           const PM& pm, int row0) {
   using TL = Tile<Tin, R>;
 #pragma unroll
   for (int j = 0; j < TL::kPieces; ++j) {

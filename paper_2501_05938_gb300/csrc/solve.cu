@@ -11,11 +11,24 @@
 
 #include "onchip.cuh"
 #include "tps_internal.h"
+#include "window_kernels.cuh"
 
 namespace tps {
 
 size_t onchip_exchange_bytes() { return (size_t)4 * 2 * kOcMaxCtas * 8; }
 int truncate_rows_max() { return kWinRowsMax; }
+int truncate_warp_mb(int R, int h) {
+  const int64_t e = (int64_t)R + 2 * (int64_t)h;
+  if (R < 2 || h < 0 || e % 32) return 0;
+  const int mb = (int)(e / 32);
+  return (mb >= kWinBlockMin && mb <= kWinBlockMax) ? mb : 0;
+}
+size_t truncate_rel_bytes(int64_t n_max, int R, int h, int dtype) {
+  const int mb = truncate_warp_mb(R, h);
+  if (mb == 0 || n_max <= 0) return 0;
+  const int64_t windows = (n_max + R - 1) / R;
+  return (size_t)windows * win_rel_rows(mb) * 96 * elem_bytes_red(dtype);
+}
 
 // ------------------------------------------------------------------ on-chip solve
 struct OcGeom {
@@ -590,13 +603,47 @@ static cudaError_t launch_window(tps_plan_s* P, int64_t n, const Tin* a, const T
   return cudaGetLastError();
 }
 
+// One warp per window (k_wsolve): R + 2 h = 32 mb.
+template <class Ar, class Tin, class Tred>
+static cudaError_t launch_wsolve(tps_plan_s* P, int64_t n, int mb, const Tin* a, const Tin* b,
+                                 const Tin* c, const Tin* d, Tin* x, cudaStream_t s) {
+  using T = typename Ar::T;
+  const int R = P->m, h = P->m_reduced;
+  constexpr int kVec = 16 / (int)sizeof(Tin);
+  const uintptr_t al = (uintptr_t)a | (uintptr_t)b | (uintptr_t)c | (uintptr_t)d | (uintptr_t)x;
+  const bool vec = (al % 16) == 0 && mb % kVec == 0 && R % kVec == 0 && h % kVec == 0;
+  unsigned* bound = reinterpret_cast<unsigned*>(P->ws + 8);
+  cudaError_t e = cudaMemsetAsync(bound, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  const float tol = (float)(P->desc.tol > 0.0 ? P->desc.tol : 1e-12);
+  Tred* rel = reinterpret_cast<Tred*>(P->ws + P->off_rel);
+  const unsigned windows = (unsigned)((n + R - 1) / R);
+  constexpr size_t smem = WinSmem<Tin, Tred, T>::kBytes;
+  if (vec)
+    k_wsolve<Ar, Tin, Tred, true><<<windows, 32, smem, s>>>(n, R, h, mb, a, b, c, d, x, rel, tol,
+                                                            bound, P->d_status, level0_dmax(P));
+  else
+    k_wsolve<Ar, Tin, Tred, false><<<windows, 32, smem, s>>>(n, R, h, mb, a, b, c, d, x, rel, tol,
+                                                             bound, P->d_status, level0_dmax(P));
+  return cudaGetLastError();
+}
+
 tps_status run_truncated(tps_plan_s* P, int64_t n, const void* a, const void* b, const void* c,
                          const void* d, void* x, cudaStream_t s) {
   P->last_onchip = 0;
   P->last_levels = 0;
   cudaError_t e = cudaSuccess;
+  const int mb = truncate_warp_mb(P->m, P->m_reduced);
   if (n <= kBaseMax) {
     e = base_solve(P, n, a, b, c, d, x, s, nullptr, 0);
+  } else if (mb > 0) {
+    e = dispatch(P->desc.dtype, [&](auto ar, auto* tin, auto* tred) -> cudaError_t {
+      using Ar = decltype(ar);
+      using Tin = std::remove_pointer_t<decltype(tin)>;
+      using Tred = std::remove_pointer_t<decltype(tred)>;
+      return launch_wsolve<Ar, Tin, Tred>(P, n, mb, (const Tin*)a, (const Tin*)b, (const Tin*)c,
+                                          (const Tin*)d, (Tin*)x, s);
+    });
   } else {
     e = dispatch(P->desc.dtype, [&](auto ar, auto* tin, auto* tred) -> cudaError_t {
       using Ar = decltype(ar);

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "tps_internal.h"
+#include "window_kernels.cuh"
 
 namespace tps {
 
@@ -82,7 +83,10 @@ static size_t workspace_for(tps_plan_s* P, size_t* off_levels_out, size_t* off_d
   P->off_xch = off;          // interface rows of the on-chip solve
   off = align_up(off + onchip_exchange_bytes());
   *off_levels_out = off;
-  if (P->desc.flags & TPS_TRUNCATE) {  // windows are solved on chip: no levels
+  if (P->desc.flags & TPS_TRUNCATE) {  // windows are solved on their own: no levels
+    P->off_rel = off;
+    off = align_up(off + truncate_rel_bytes(P->desc.n_max, P->m, P->m_reduced, P->desc.dtype));
+    *off_levels_out = off;
     *off_dev_out = off;
     return off;
   }
@@ -153,7 +157,8 @@ tps_status tps_plan(const tps_plan_desc* desc, tps_plan_t* out) {
     // windows of m kept rows and m_reduced halo rows (both even, 0 = choose)
     if (d.residency != TPS_DEVICE || d.dtype == TPS_MIXED_F32_F64) return TPS_ERR_UNSUPPORTED;
     if ((d.m % 2) || (d.m_reduced % 2) || d.m_reduced < 0) return TPS_ERR_INVALID_ARG;
-    if ((int64_t)d.m + 2 * (int64_t)d.m_reduced > truncate_rows_max())
+    if ((int64_t)d.m + 2 * (int64_t)d.m_reduced > truncate_rows_max() &&
+        !(d.m > 0 && truncate_warp_mb(d.m, d.m_reduced) > 0))
       return TPS_ERR_INVALID_ARG;
   }
   if ((d.flags & TPS_ZERO_COPY) && d.residency != TPS_HOST_PINNED) return TPS_ERR_INVALID_ARG;
@@ -189,7 +194,10 @@ tps_status tps_plan(const tps_plan_desc* desc, tps_plan_t* out) {
       h += h & 1;
       P->m_reduced = std::min(std::max(h, 2), truncate_rows_max() / 4);
     }
-    if (P->m == 0) P->m = (truncate_rows_max() - 2 * P->m_reduced) & ~1;
+    // the one-warp windows: 32 blocks of kWinBlockMax rows per extended
+    // window (the fastest measured: the window's fixed costs -- halo,
+    // 64-row interface solve, bound -- spread over the most rows)
+    if (P->m == 0) P->m = 32 * kWinBlockMax - 2 * P->m_reduced;
     if (P->m < 2) {
       delete P;
       return TPS_ERR_INVALID_ARG;

@@ -97,6 +97,8 @@ struct tps_plan_s {
   int32_t sg_onchip = 0, sg_levels = 0;
   // TPS_ZERO_COPY: the device can read and write pageable host memory
   bool pageable_ok = false;
+  // one-warp windowed solve (TPS_TRUNCATE): its relation buffer
+  size_t off_rel = 0;
   // on-chip solve: exchange rows for the CTAs' interface equations, and
   // which part of the last solve ran on chip (0 none, 1 all, 2 reduced)
   size_t off_xch = 0;
@@ -154,8 +156,14 @@ cudaError_t onchip_solve(int dtype, int64_t n, const void* a, const void* b, con
 // TPS_TRUNCATE: the windowed solve of one device-resident system.
 tps_status run_truncated(tps_plan_s* P, int64_t n, const void* a, const void* b, const void* c,
                          const void* d, void* x, cudaStream_t s);
-// Largest extended window (kept rows + both halos) of the windowed solve.
+// Largest extended window (kept rows + both halos) of the one-CTA windowed
+// solve.
 int truncate_rows_max();
+// Rows per lane block of the one-warp windowed solve for R kept rows and h
+// halo rows (R + 2 h = 32 mb), or 0 when that solve does not apply.
+int truncate_warp_mb(int R, int h);
+// Bytes of the one-warp windowed solve's relation buffer for n_max rows.
+size_t truncate_rel_bytes(int64_t n_max, int R, int h, int dtype);
 // Copy `bytes` between host and device memory with a streaming kernel (SM
 // loads and stores, no copy engine); either side may be host memory the
 // device can address.  bytes and both pointers: multiples of 4.

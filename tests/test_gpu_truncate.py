@@ -50,6 +50,45 @@ def test_matches_the_truncation_oracle(dtype, n, R, h):
     assert info["status_name"] == expect
 
 
+# R + 2 h = 32 mb: the one-warp windows (mb = 8, 16, 56, 64, 256; a clipped
+# one-row block at the end for n = 1865 and 300001; one window for n = 65, 1000)
+WARP_CASES = [(65, 2040, 4), (1000, 2040, 4), (1865, 1840, 104), (100003, 1840, 104),
+              (262144, 1840, 104), (300001, 1840, 104), (70001, 240, 8), (20003, 480, 16),
+              (70001, 1024, 384), (1_000_003, 7984, 104), (4099, 1744, 152)]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f64_df", "f32"])
+@pytest.mark.parametrize("n,R,h", WARP_CASES)
+def test_warp_windows_match_the_truncation_oracle(dtype, n, R, h):
+    """The one-warp windows (each lane a block of mb rows, the partition
+    method inside the warp): the oracle's windows element by element, its
+    bound, and the same bits on a second solve (the relation buffer is
+    discarded from L2 after each use)."""
+    s = synth.system(700 + n + h, n)
+    tdt = torch.float64
+    if dtype == "f32":
+        s, tdt = synth.to_f32(s), torch.float32
+    a, b, c, d = (np.asarray(s[k], dtype=np.float64) for k in "abcd")
+    xr, br = TR.truncated(a, b, c, d, R, h)
+    plan = binding.Plan(n, dtype=dtype, m=R, m_reduced=h, tol=1.0, flags=binding.TRUNCATE)
+    x, info = run(plan, s, tdt)
+    x2, info2 = run(plan, s, tdt)
+    np.testing.assert_array_equal(x2, x)
+    tol = 1e-5 if dtype == "f32" else 1e-11
+    assert oracle.rel_forward_error(x, xr) <= tol
+    bmax = float(np.max(br))
+    if bmax > 1e-30:
+        assert bmax * (1 - 1e-4) <= info["last_correction"] <= bmax * 1.01
+    else:
+        assert info["last_correction"] <= 1e-30
+    expect = "TPS_OK" if bmax <= 1.0 else "TPS_ERR_NO_CONVERGENCE"
+    assert info["status_name"] == expect
+    if dtype != "f32" and bmax <= 1e-12:
+        ref = oracle.thomas(a, b, c, d)
+        assert oracle.rel_forward_error(x, ref) <= 1e-10
+        assert oracle.rel_residual(a, b, c, d, x) <= 1e-12
+
+
 def test_bound_over_tolerance_is_reported():
     n = 20000
     s = synth.system(9, n)
@@ -68,7 +107,8 @@ def test_chosen_parameters_meet_the_tolerance(dtype):
     x, info = run(plan, s)
     assert info["status"] == 0 and info["last_correction"] <= 1e-12
     assert info["m"] % 2 == 0 and info["m_reduced"] % 2 == 0
-    assert info["m"] + 2 * info["m_reduced"] <= 1792
+    # the default windows are one-warp windows of 32 blocks of 256 rows
+    assert info["m"] + 2 * info["m_reduced"] == 8192
     ref = oracle.thomas(s["a"], s["b"], s["c"], s["d"])
     assert oracle.rel_forward_error(x, ref) <= 1e-10
     assert oracle.rel_residual(s["a"], s["b"], s["c"], s["d"], x) <= 1e-12
