@@ -77,6 +77,17 @@ struct ArF64 {
   }
   __device__ __forceinline__ static bool out_bad(double v);
   __device__ __forceinline__ static bool out_bad(float) { return false; }
+  // k_stage1 skips the first unknown's decayed chain (a second unrolled
+  // chunk body): worth it where the fp64 pipe bounds the kernel (measured:
+  // Stage 1 2.64 -> 1.97 ms at n = 2^27); the fp32-pipe policies keep one
+  // body (the second one cost more in instruction fetch than it saved)
+  static constexpr bool kSkipChain = true;
+  // |x| below 2^-60 (a decayed product chain, see k_stage1)
+  __device__ __forceinline__ static bool chain_small(T x) { return fabs(x) < 0x1p-60; }
+  // |c| <= |beta| to about 2^-20, on the high words (integer pipe)
+  __device__ __forceinline__ static bool mag_le(T c, T beta) {
+    return ((unsigned)__double2hiint(c) & 0x7FFFFFFFu) <= ((unsigned)__double2hiint(beta) & 0x7FFFFFFFu);
+  }
 };
 
 // ------------------------------------------------------------------ fp32
@@ -127,6 +138,9 @@ struct ArF32 {
     return (__float_as_uint(v) & 0x7F800000u) == 0x7F800000u;
   }
   __device__ __forceinline__ static bool out_bad(double v);
+  static constexpr bool kSkipChain = false;
+  __device__ __forceinline__ static bool chain_small(T x) { return fabsf(x) < 0x1p-30f; }
+  __device__ __forceinline__ static bool mag_le(T c, T beta) { return fabsf(c) <= fabsf(beta); }
 };
 
 // ------------------------------------------------------------------ double-float
@@ -478,6 +492,11 @@ struct ArDF {
   }
   __device__ __forceinline__ static bool out_bad(double v) { return x_out_of_range_df(v); }
   __device__ __forceinline__ static bool out_bad(float2) { return false; }
+  static constexpr bool kSkipChain = false;
+  __device__ __forceinline__ static bool chain_small(T x) { return fabsf(x.hi) < 0x1p-60f; }
+  __device__ __forceinline__ static bool mag_le(T c, T beta) {
+    return fabsf(c.hi) <= fabsf(beta.hi);
+  }
 };
 
 }  // namespace tps

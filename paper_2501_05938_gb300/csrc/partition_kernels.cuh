@@ -43,6 +43,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "arith.cuh"
 
 namespace tps {
@@ -365,20 +367,33 @@ __global__ void __launch_bounds__(W * 32)
   RowChk chk;
   int64_t sys = lv.nbnd > 0 && active ? bd.first : 0;
 
+  // The first interior unknown's chain (P, Q, S) only adds terms scaled by
+  // S, whose magnitude falls by |c / beta| < 1 every row of a strictly
+  // diagonally dominant block.  Where the policy allows (Ar::kSkipChain),
+  // once every lane's |S| is below 2^-60 the rest of the chain is below
+  // rounding and the rows skip it (kChain false); they check |c| <= |beta|
+  // instead, so S cannot grow back, and a block where that fails reports a
+  // pivot failure (not dominant).
+  bool chain = true, nondom = false;
+
   // one interior row (1 <= row <= L-2).  The product chains alpha and S and
   // the accumulators P and Q are left unnormalised here and renormalised
   // once per chunk (renorm), which bounds their low parts to a few ulps.
-  auto interior = [&](const T av, const T bv, const T cv, const T dv) {
+  auto interior = [&](const T av, const T bv, const T cv, const T dv, auto kChain) {
     const T ratio = Ar::mul_nn(av, rbp);
     beta = Ar::sub_mul_dom(bv, ratio, cprev);
     g = Ar::sub_mul(dv, ratio, g);
     al = Ar::mul_neg_nn(ratio, al);
     bad |= Ar::bad_pivot(beta);
     const T rbeta = Ar::rcp(beta);
-    const T tt = Ar::mul_nn(S, rbeta);
-    P = Ar::sub_mul_nn(P, tt, g);
-    Q = Ar::sub_mul_nn(Q, tt, al);
-    S = Ar::mul_neg_nn(tt, cv);
+    if constexpr (decltype(kChain)::value) {
+      const T tt = Ar::mul_nn(S, rbeta);
+      P = Ar::sub_mul_nn(P, tt, g);
+      Q = Ar::sub_mul_nn(Q, tt, al);
+      S = Ar::mul_neg_nn(tt, cv);
+    } else {
+      nondom |= !Ar::mag_le(cv, beta);
+    }
     rbp = rbeta;
     cprev = cv;
   };
@@ -408,9 +423,10 @@ __global__ void __launch_bounds__(W * 32)
     const Tin* t = tile + (ch & 1) * TL::kBuf + lane * TL::kStride;
     const bool clean = !__any_sync(0xffffffffu, bd.cnt > 0 && bd.touches(start + row0, R));
     const int kind = chunk_kind(ch, row0, R, lmin, luni, clean);
-    if (kind != kSlow) {
-      // one unrolled body for the three kinds: only row 0 and row R-1 test
-      // (warp-uniformly) whether they are the block's f or l row
+    // one unrolled body for the three kinds (only row 0 and row R-1 test,
+    // warp-uniformly, whether they are the block's f or l row), compiled
+    // with and without the first unknown's chain
+    auto fast_chunk = [&](auto kChain) {
       const bool first = kind == kFirst, last = kind == kLast;
 #pragma unroll
       for (int r = 0; r < R; r += V) {
@@ -433,12 +449,20 @@ __global__ void __launch_bounds__(W * 32)
             al = Ar::mul_neg_nn(ratio, al);
             clast = cv;
           } else {
-            interior(av, bv, cv, dv);
+            interior(av, bv, cv, dv, kChain);
             if constexpr (R > K) {  // chunk spans several checkpoint intervals
               if ((rr + 1) % K == 0 && rr + 1 < R) checkpoint(row0 + rr);
             }
           }
         }
+      }
+    };
+    if (kind != kSlow) {
+      if constexpr (Ar::kSkipChain) {
+        if (chain) fast_chunk(std::true_type{});
+        else fast_chunk(std::false_type{});
+      } else {
+        fast_chunk(std::true_type{});
       }
     } else {
 #pragma unroll 1
@@ -463,7 +487,8 @@ __global__ void __launch_bounds__(W * 32)
           if (row == 0) {
             a0 = av; b0 = bv; c0 = cv; d0 = dv;
           } else if (row < L - 1) {
-            interior(av, bv, cv, dv);
+            if (!Ar::kSkipChain || chain) interior(av, bv, cv, dv, std::true_type{});
+            else interior(av, bv, cv, dv, std::false_type{});
             if constexpr (R > K) {
               if ((row + 1) % K == 0 && r + 1 < R) checkpoint(row);
             }
@@ -481,8 +506,12 @@ __global__ void __launch_bounds__(W * 32)
     // the checkpoint at the chunk's end (row0 + R is a multiple of K when
     // K divides R, and every K / R chunks otherwise)
     if (((row0 + R) % K) == 0) checkpoint(row0 + R - 1);
+    if constexpr (Ar::kSkipChain) {
+      if (chain && __all_sync(0xffffffffu, !active || Ar::chain_small(S))) chain = false;
+    }
     __syncwarp();  // the buffer is refilled by the next iteration's copies
   }
+  bad |= nondom;
   if (active) {
     bad |= Ar::bad_pivot(beta);
     if (L == 1) {
