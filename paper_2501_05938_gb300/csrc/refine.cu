@@ -87,8 +87,17 @@ tps_status run_refine(tps_plan_s* P, int64_t n, const double* a, const double* b
   const double tol = P->desc.tol > 0.0 ? P->desc.tol : 1e-12;
   P->last_iters = 0;
   P->last_corr = 0.0;
+  // the first solve carries the range codes of the system (an fp32 x0 of a
+  // right-hand side below the pairs' range would be 0 and 'converge'); the
+  // corrections' right-hand sides are small by construction and skip them
+  struct CodesOn {
+    tps_plan_s* P;
+    ~CodesOn() { P->codes_off = false; }
+  } restore{P};
+  P->codes_off = false;
   tps_status st = run_solve(P, n, a, b, c, d, x, s, lv, nullptr, bnd, nbnd);
   if (st != TPS_OK) return st;
+  P->codes_off = true;
   for (int it = 1; it <= max_iters; ++it) {
     k_residual<<<grid_for(n), 256, 0, s>>>(n, a, b, c, d, x, r, bnd, nbnd);
     if (cudaGetLastError() != cudaSuccess) return TPS_ERR_CUDA;

@@ -128,8 +128,9 @@ static cudaError_t launch_onchip(tps_plan_s* P, int64_t n, const Tin* a, const T
 }
 
 unsigned* level0_dmax(tps_plan_s* P) {
-  return P->desc.dtype == TPS_F64_DF ? reinterpret_cast<unsigned*>(P->ws + P->off_dmax)
-                                     : nullptr;
+  const bool on = P->desc.dtype == TPS_F64_DF ||
+                  (P->desc.dtype == TPS_MIXED_F32_F64 && !P->codes_off);
+  return on ? reinterpret_cast<unsigned*>(P->ws + P->off_dmax) : nullptr;
 }
 
 cudaError_t dcode_check(tps_plan_s* P, int64_t count, cudaStream_t s) {

@@ -68,9 +68,13 @@ struct tps_plan_s {
   size_t ws_bytes = 0, ws_needed = 0;
   bool ws_owned = false;
   int* d_status = nullptr;     // device status word (first bytes of ws)
-  // per-system range codes of the last solve's rows (double-float plans;
-  // kCodes x max(1, batch_max) words after the header), zero between solves
+  // per-system range codes of the last solve's rows (double-float plans and
+  // the first fp32 solve of a mixed one; kCodes x max(1, batch_max) words
+  // after the header), zero between solves
   size_t off_dmax = 0;
+  // the mixed solve's corrections (right-hand sides small by construction)
+  // skip the range codes
+  bool codes_off = false;
   double* d_scalars = nullptr; // refinement reductions (next bytes of ws)
   size_t off_levels = 0;       // first level buffer offset
   size_t off_refine = 0;       // refinement residual and correction vectors

@@ -17,7 +17,13 @@
            RMSE on a shuffled 3:1 split, and the rule's stream counts against
            the measured optimum per size; writes paper_models_gb300.json
 
+  solve    repeated solves of one synthetic system with given parameters
+           (for a profiler to capture, or a quick timing of one setting):
+           solve [--n N] [--dtype f64_df] [--m M] [--m-reduced H]
+                 [--truncate] [--no-onchip] [--repeat K]
+
 Usage: python -m paper_2501_05938_gb300.tune collect|train|evaluate|paper|all [dir]
+       python -m paper_2501_05938_gb300.tune solve [options]
 """
 from __future__ import annotations
 
@@ -515,8 +521,47 @@ def paper_models(rows, dtype=0, seed=SPLIT_SEED, split=1e6):
             "overhead_small": ov_fit["small"], "overhead_big": ov_fit["big"], "table": table}
 
 
+def solve_cmd(args):
+    """K solves of one paper system (device generator) with the given plan
+    parameters; prints the last solve's mean time and the plan's report."""
+    import argparse
+
+    import torch
+
+    from . import binding, synth
+
+    ap = argparse.ArgumentParser(prog="tune solve")
+    ap.add_argument("--n", type=int, default=1 << 24)
+    ap.add_argument("--dtype", default="f64_df", choices=list(binding.DTYPES))
+    ap.add_argument("--m", type=int, default=0)
+    ap.add_argument("--m-reduced", type=int, default=0)
+    ap.add_argument("--truncate", action="store_true")
+    ap.add_argument("--no-onchip", action="store_true")
+    ap.add_argument("--repeat", type=int, default=3)
+    a = ap.parse_args(args)
+    g = synth.system_device(1002, a.n)
+    tdt = torch.float32 if a.dtype == "f32" else torch.float64
+    arrs = [g[k].to(tdt) for k in "abcd"]
+    x = torch.empty_like(arrs[1])
+    flags = (binding.TRUNCATE if a.truncate else 0) | (binding.NO_ONCHIP if a.no_onchip else 0)
+    plan = binding.Plan(a.n, dtype=a.dtype, m=a.m, m_reduced=a.m_reduced, flags=flags)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.repeat):
+        plan.solve(*arrs, x)
+    e1.record()
+    torch.cuda.synchronize()
+    info = plan.query()
+    print(json.dumps({"n": a.n, "dtype": a.dtype, "ms_per_solve": e0.elapsed_time(e1) / a.repeat,
+                      "status": info["status_name"], "m": info["m"],
+                      "m_reduced": info["m_reduced"], "bound": info["last_correction"]}))
+    return 0 if info["status"] == 0 else 1
+
+
 def main(argv):
     cmd = argv[1] if len(argv) > 1 else "all"
+    if cmd == "solve":
+        sys.exit(solve_cmd(argv[2:]))
     out = argv[2] if len(argv) > 2 else PRED_DIR
     os.makedirs(out, exist_ok=True)
     csv_path = os.path.join(out, "timings_gb300.csv")

@@ -294,3 +294,16 @@ def test_noalloc_range():
         assert st.item() == want
         if want == 0:
             assert_matches(t, x.cpu().numpy())
+
+
+@pytest.mark.parametrize("e,want", [(-40, "TPS_OK"), (40, "TPS_OK"), (-100, "TPS_ERR_RANGE")])
+def test_mixed_refinement_range(e, want):
+    """The mixed solve's first fp32 elimination carries the same range codes:
+    a right-hand side below what it can represent is reported instead of
+    'converging' to x = 0; inside the range it refines to the fp64 bar."""
+    n = 100003
+    s = scaled(synth.system(85, n), rhs=2.0 ** e)
+    x, info = solve(s, dtype="mixed")
+    assert info["status_name"] == want, info
+    if want == "TPS_OK":
+        assert_matches(s, x)
