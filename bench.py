@@ -737,7 +737,9 @@ def main():
     traffic = tt.get(f"{dominant}_f64_df_m{info['m']}", tt.get(f"{dominant}_f64_df"))
     kernel_hash = kernel_source_hash()
     levels = info["levels"]
-    launches_per_step = 2 * levels + 1
+    # Stage 1 and Stage 3 per level, the base solve, and the range-code check
+    # after level 0's Stage 1 (double-float only)
+    launches_per_step = 2 * levels + 2
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

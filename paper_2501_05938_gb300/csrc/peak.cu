@@ -19,7 +19,9 @@ __global__ void __launch_bounds__(kThreads) k_fp64_op(double* __restrict__ out, 
   double v[kChains];
 #pragma unroll
   for (int k = 0; k < kChains; ++k) v[k] = 1.0 + 1e-3 * (double)(threadIdx.x + k);
-  const double mul = 0.9999999, add = 1e-9;
+  // operands in registers (not constants), as in the solver's kernels
+  const double mul = 0.9999999 + 1e-13 * (double)(threadIdx.x & 3);
+  const double add = 1e-9 * (double)(1 + (threadIdx.x & 1));
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
     for (int k = 0; k < kChains; ++k) {
