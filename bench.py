@@ -678,13 +678,20 @@ def main():
         infoh = plan_h.query()
         eh_err = max((h.to("cuda") - g["x_true"]).abs().max().item() for h in hxs) \
             / g["x_true"].abs().max().item()
-        # one system per call (tps_solve_host_async): no overlap between steps
-        _, single_ms = time_host(plan_h, hk, hx, stream, esteps, min(a.warmup, 3), world)
-        # the predictor's (S, chunk) without the search, the same single calls
+        # one system per call (tps_solve_host_async): no overlap between
+        # steps; beside it the predictor's (S, chunk) without the search, the
+        # same single calls.  The two alternate over three rounds (the link is
+        # shared, its speed drifts) and each reports its median round.
         plan_hp = binding.Plan(n, dtype="f64_df", residency="host", m=infoh["m"],
                                m_reduced=a.m_reduced, streams=pred_h["streams"],
                                chunk=pred_h["chunk"])
-        _, single_ms_pred = time_host(plan_hp, hk, hx, stream, esteps, min(a.warmup, 3), world)
+        singles, singles_pred = [], []
+        for _ in range(3):
+            singles.append(time_host(plan_h, hk, hx, stream, esteps, min(a.warmup, 3), world)[1])
+            singles_pred.append(
+                time_host(plan_hp, hk, hx, stream, esteps, min(a.warmup, 3), world)[1])
+        single_ms = statistics.median(singles)
+        single_ms_pred = statistics.median(singles_pred)
         del plan_hp
         floor_ms, h2d_ms = link_floor(hk, hx, g, x, stream)
         del plan_h
@@ -768,9 +775,9 @@ def main():
                       "ms_predicted": ms_pred, "ms_autotuned": ms,
                       "regret_live": ms_pred / ms - 1.0,
                       "host": {"predicted": {"streams": pred_h["streams"], "chunk": pred_h["chunk"],
-                                             "ms": single_ms_pred},
+                                             "ms": single_ms_pred, "rounds_ms": singles_pred},
                                "autotuned": {"streams": infoh["streams"], "chunk": infoh["chunk"],
-                                             "ms": single_ms},
+                                             "ms": single_ms, "rounds_ms": singles},
                                "regret_live": single_ms_pred / single_ms - 1.0},
                       "note": "T(prediction) / T(exhaustive search's choice) - 1, both timed "
                               "here on the same arrays (negative: the search's pick measured "

@@ -140,6 +140,9 @@ typedef struct {
                          /* accepted (the device reads it coherently), else 0     */
   int32_t onchip;        /* last solve: 0 all levels by separate launches; 1 the   */
                          /* whole system, 2 its reduced system, solved on chip     */
+  int32_t refine_fused;  /* last mixed solve: 1 if its corrections ran fused into   */
+                         /* level 0's Stage 1 / Stage 3 (residual formed in Stage 1, */
+                         /* x += delta in Stage 3), 0 as separate passes            */
 } tps_info;
 
 /* Create a plan.  Validates `desc` (n_max >= 0, dtype, m 0 or >= 2, streams

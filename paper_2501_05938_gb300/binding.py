@@ -44,7 +44,8 @@ class Info(ctypes.Structure):
                 ("streams", ctypes.c_int32), ("levels", ctypes.c_int32),
                 ("chunk", ctypes.c_int64), ("last_correction", ctypes.c_double),
                 ("stage_ms", ctypes.c_float * 4), ("workspace_bytes", ctypes.c_size_t),
-                ("pageable_ok", ctypes.c_int32), ("onchip", ctypes.c_int32)]
+                ("pageable_ok", ctypes.c_int32), ("onchip", ctypes.c_int32),
+                ("refine_fused", ctypes.c_int32)]
 
 
 class TpsError(RuntimeError):
@@ -236,7 +237,8 @@ class Plan:
                 "streams": info.streams, "levels": info.levels, "chunk": info.chunk,
                 "last_correction": info.last_correction,
                 "stage_ms": list(info.stage_ms), "workspace_bytes": info.workspace_bytes,
-                "pageable_ok": bool(info.pageable_ok), "onchip": info.onchip}
+                "pageable_ok": bool(info.pageable_ok), "onchip": info.onchip,
+                "refine_fused": bool(info.refine_fused)}
 
 
 def measure_fp64_rates():

@@ -187,23 +187,65 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 
 // ------------------------------------------------------------------ warp tile
-template <class Tin, int R>
+// NA arrays per buffer: a, b, c, d, and for a refinement step (RefineIO) the
+// current x as a fifth.
+template <class Tin, int R, int NA = 4>
 struct Tile {
   static constexpr int kVec = 16 / (int)sizeof(Tin);  // elements per 16-byte piece
   static_assert(R % kVec == 0, "chunk rows must fill 16-byte pieces");
   static constexpr int kPieces = R / kVec;            // pieces per block and chunk
   static constexpr int kStride = R + kVec;            // padded block slot (16-byte multiple)
   static constexpr int kArr = 32 * kStride;           // one array of one buffer
-  static constexpr int kBuf = 4 * kArr;               // a, b, c, d
+  static constexpr int kBuf = NA * kArr;
   static constexpr size_t kBytesPerWarp = sizeof(Tin) * 2 * kBuf;
 };
 
 // Stage 3 also prefetches each chunk's checkpoint (three values per block)
 // with the chunk: per buffer, 3 x 32 values after the warp's two buffers.
-template <class Tin, class Tred, int R>
-struct Tile3 : Tile<Tin, R> {
+template <class Tin, class Tred, int R, int NA = 4>
+struct Tile3 : Tile<Tin, R, NA> {
   static constexpr size_t kCkBytesPerBuf = 3 * 32 * sizeof(Tred);
-  static constexpr size_t kBytesPerWarp = Tile<Tin, R>::kBytesPerWarp + 2 * kCkBytesPerBuf;
+  static constexpr size_t kBytesPerWarp = Tile<Tin, R, NA>::kBytesPerWarp + 2 * kCkBytesPerBuf;
+};
+
+// One correction step of mixed-precision iterative refinement, fused into
+// the level-0 sweeps (kRef kernels; fp64 arrays).  Stage 1 forms the
+// residual r = d - A x of the current iterate in fp64 while it streams the
+// rows, eliminates with r as the right-hand side and writes r out; Stage 3,
+// given r as its right-hand side, adds the correction delta to x in place
+// and raises max2[0] = max |delta|, max2[1] = max |x + delta|, each as the
+// bit pattern of a non-negative double (which orders like the value; a NaN
+// ranks above +inf).
+struct RefineIO {
+  const double* x;          // Stage 1: the current iterate (read with its neighbours)
+  double* r;                // Stage 1: the residual, written
+  unsigned long long* max2; // Stage 3: the two maxima (zeroed before the launch)
+};
+
+// Pieces of the current x a Stage-1 refinement chunk needs: its R rows and
+// the next piece (the row below the chunk), i.e. kPieces + 1 pieces filling
+// the block's padded slot; piece q = lane + 32 j (j <= kPieces) is piece
+// q % (kPieces + 1) of block q / (kPieces + 1).
+template <class Tin, int R>
+struct XPieceMap {
+  using TL = Tile<Tin, R>;
+  static constexpr int kP = TL::kPieces + 1;
+  int64_t goff[kP];
+  int soff[kP];
+  int row[kP];
+  int len[kP];
+  __device__ __forceinline__ void init(const Level& lv, int64_t k0, int nb, int lane) {
+#pragma unroll
+    for (int j = 0; j < kP; ++j) {
+      const int q = lane + 32 * j;
+      const int blk = q / kP;
+      const int pc = q % kP;
+      row[j] = pc * TL::kVec;
+      len[j] = blk < nb ? block_len(lv, k0 + blk) : 0;
+      goff[j] = (k0 + blk) * (int64_t)lv.m + row[j];
+      soff[j] = blk * TL::kStride + row[j];
+    }
+  }
 };
 
 // 16 bytes of consecutive rows (one 128-bit shared access).
@@ -289,6 +331,40 @@ __device__ __forceinline__ void store_chunk(Tin* __restrict__ x, const Tin* buf,
   }
 }
 
+// Rows [row0, row0 + R] of the current x for the warp's blocks: every row up
+// to and including the one below the block (the next block's first row),
+// clipped to the array's n rows.
+template <class Tin, int R, bool kVec16>
+__device__ __forceinline__ void load_xchunk(Tin* buf, const Tin* x, const XPieceMap<Tin, R>& xm,
+                                            int row0, int64_t n) {
+  using TL = Tile<Tin, R>;
+#pragma unroll
+  for (int j = 0; j < XPieceMap<Tin, R>::kP; ++j) {
+    if (xm.len[j] == 0) continue;
+    const int64_t g = xm.goff[j] + row0;
+    const int64_t avail = min((int64_t)(xm.len[j] + 1 - (row0 + xm.row[j])), n - g);
+    if (kVec16 && avail >= TL::kVec) {
+      cp_async<16>(buf + xm.soff[j], x + g);
+    } else if (avail > 0) {
+#pragma unroll
+      for (int v = 0; v < TL::kVec; ++v)
+        if (v < avail) cp_async<sizeof(Tin)>(buf + xm.soff[j] + v, x + g + v);
+    }
+  }
+}
+
+// r = d - (a x_{i-1} + b x_i + c x_{i+1}) in fp64 (a and c already cut to
+// zero where a coupling does not exist, and the matching x passed as 0).
+__device__ __forceinline__ double residual_row(double a, double b, double c, double d, double xm,
+                                               double x0, double xp) {
+  double r = fma(-b, x0, d);
+  r = fma(-a, xm, r);
+  return fma(-c, xp, r);
+}
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+}
+
 // chunks the warp iterates: the longest block of the warp decides
 __device__ __forceinline__ int warp_chunks(const Level& lv, int64_t k0, int nb, int R) {
   const int lmax = (k0 + nb == lv.p) ? max(lv.m, lv.llast) : lv.m;
@@ -320,17 +396,19 @@ __device__ __forceinline__ int chunk_kind(int ch, int row0, int R, int lmin, int
 
 // ------------------------------------------------------------------ Stage 1
 // R rows per chunk; a checkpoint every K rows (K the chunk length of
-// Stage 3; one of R and K divides the other).
-template <class Ar, class Tin, class Tred, int R, int K, int W, bool kVec16>
+// Stage 3; one of R and K divides the other).  kRef: a refinement step
+// (RefineIO), the right-hand side being the residual of rf.x.
+template <class Ar, class Tin, class Tred, int R, int K, int W, bool kVec16, bool kRef = false>
 __global__ void __launch_bounds__(W * 32)
     k_stage1(Level lv, const Tin* __restrict__ a, const Tin* __restrict__ b,
              const Tin* __restrict__ c, const Tin* __restrict__ d, Tred* __restrict__ ra,
              Tred* __restrict__ rb, Tred* __restrict__ rc, Tred* __restrict__ rd,
              Tred* __restrict__ ck_gam, Tred* __restrict__ ck_y, Tred* __restrict__ ck_v,
-             int* __restrict__ status) {
+             int* __restrict__ status, RefineIO rf = {}) {
   using T = typename Ar::T;
-  using TL = Tile<Tin, R>;
+  using TL = Tile<Tin, R, kRef ? 5 : 4>;
   constexpr int V = TL::kVec;
+  static_assert(!kRef || std::is_same<Tin, double>::value, "refinement steps are fp64");
   static_assert(R % K == 0 || K % R == 0, "chunk rows and checkpoint spacing must nest");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -349,10 +427,21 @@ __global__ void __launch_bounds__(W * 32)
   PieceMap<Tin, R> pm;
   pm.init(lv, k0, nb, lane);
   load_chunk<Tin, R, kVec16>(tile, srcs, 4, pm, 0);
+  XPieceMap<Tin, R> xpm;
+  if constexpr (kRef) {
+    xpm.init(lv, k0, nb, lane);
+    load_xchunk<Tin, R, kVec16>(tile + 4 * TL::kArr, (const Tin*)rf.x, xpm, 0, lv.n);
+  }
   cp_async_commit();
   const int64_t start = k * (int64_t)lv.m;
   Bounds bd;
   bd.init(lv, start, L, active);
+  // refinement: x of the row above the current one (the previous block's
+  // last row before the block's first row)
+  Tin xup = Tin{};
+  if constexpr (kRef) {
+    if (active && start > 0) xup = rf.x[start - 1];
+  }
 
   // virtual state before row 1 (relation x_0 = f): rbeta = 1, c_prev = 0,
   // g = 0, alpha = -1; first interior unknown x_1 = P - Q f - S x_1 with
@@ -416,11 +505,17 @@ __global__ void __launch_bounds__(W * 32)
 
   for (int ch = 0; ch < nch; ++ch) {
     const int row0 = ch * R;
-    if (ch + 1 < nch) load_chunk<Tin, R, kVec16>(tile + ((ch + 1) & 1) * TL::kBuf, srcs, 4, pm, row0 + R);
+    if (ch + 1 < nch) {
+      Tin* nxt = tile + ((ch + 1) & 1) * TL::kBuf;
+      load_chunk<Tin, R, kVec16>(nxt, srcs, 4, pm, row0 + R);
+      if constexpr (kRef)
+        load_xchunk<Tin, R, kVec16>(nxt + 4 * TL::kArr, (const Tin*)rf.x, xpm, row0 + R, lv.n);
+    }
     cp_async_commit();
     cp_async_wait<1>();
     __syncwarp();
-    const Tin* t = tile + (ch & 1) * TL::kBuf + lane * TL::kStride;
+    Tin* const tb = tile + (ch & 1) * TL::kBuf;
+    Tin* const t = tb + lane * TL::kStride;
     const bool clean = !__any_sync(0xffffffffu, bd.cnt > 0 && bd.touches(start + row0, R));
     const int kind = chunk_kind(ch, row0, R, lmin, luni, clean);
     // one unrolled body for the three kinds (only row 0 and row R-1 test,
@@ -436,10 +531,19 @@ __global__ void __launch_bounds__(W * 32)
         for (int v = 0; v < V; ++v) {
           const int rr = r + v;
           // a of the system's first row and c of its last are never read
+          const bool cut_c = rr == R - 1 && last && k == lv.p - 1;
           const Tin ain = (rr == 0 && first && k == 0) ? Tin{} : xa.v[v];
-          const Tin cin = (rr == R - 1 && last && k == lv.p - 1) ? Tin{} : xc.v[v];
+          const Tin cin = cut_c ? Tin{} : xc.v[v];
+          Tin din = xd.v[v];
+          if constexpr (kRef) {  // the residual of the current x
+            const Tin x0 = t[4 * TL::kArr + rr];
+            din = residual_row(ain, xb.v[v], cin, din, xup, x0,
+                               cut_c ? Tin{} : t[4 * TL::kArr + rr + 1]);
+            xup = x0;
+            t[3 * TL::kArr + rr] = din;
+          }
           T av, bv, cv, dv;
-          Ar::template row<true>(ain, xb.v[v], cin, xd.v[v], av, bv, cv, dv, chk);
+          Ar::template row<true>(ain, xb.v[v], cin, din, av, bv, cv, dv, chk);
           if (rr == 0 && first) {  // the block's first row: f's equation
             a0 = av; b0 = bv; c0 = cv; d0 = dv;
           } else if (rr == R - 1 && last) {  // the block's last row
@@ -480,10 +584,18 @@ __global__ void __launch_bounds__(W * 32)
             }
             cut_c |= bd.is(start + row + 1);
           }
+          Tin din = t[3 * TL::kArr + r];
+          if constexpr (kRef) {
+            const Tin x0 = t[4 * TL::kArr + r];
+            din = residual_row(cut_a ? Tin{} : t[r], t[TL::kArr + r],
+                               cut_c ? Tin{} : t[2 * TL::kArr + r], din, cut_a ? Tin{} : xup, x0,
+                               cut_c ? Tin{} : t[4 * TL::kArr + r + 1]);
+            xup = x0;
+            t[3 * TL::kArr + r] = din;
+          }
           T av, bv, cv, dv;
           Ar::template row<true>(cut_a ? Tin{} : t[r], t[TL::kArr + r],
-                                 cut_c ? Tin{} : t[2 * TL::kArr + r], t[3 * TL::kArr + r], av, bv,
-                                 cv, dv, chk);
+                                 cut_c ? Tin{} : t[2 * TL::kArr + r], din, av, bv, cv, dv, chk);
           if (row == 0) {
             a0 = av; b0 = bv; c0 = cv; d0 = dv;
           } else if (row < L - 1) {
@@ -508,6 +620,10 @@ __global__ void __launch_bounds__(W * 32)
     if (((row0 + R) % K) == 0) checkpoint(row0 + R - 1);
     if constexpr (Ar::kSkipChain) {
       if (chain && __all_sync(0xffffffffu, !active || Ar::chain_small(S))) chain = false;
+    }
+    if constexpr (kRef) {  // the chunk's residual (in the d slots) out
+      __syncwarp();
+      store_chunk<Tin, R, kVec16>(rf.r, tb + 3 * TL::kArr, pm, row0);
     }
     __syncwarp();  // the buffer is refilled by the next iteration's copies
   }
@@ -544,15 +660,19 @@ __global__ void __launch_bounds__(W * 32)
 }
 
 // ------------------------------------------------------------------ Stage 3
-template <class Ar, class Tin, class Tred, int R, int W, bool kVec16>
+// kRef: a refinement step (RefineIO): d is the residual Stage 1 wrote, the
+// result is added to x in place and the maxima go to rf.max2.
+template <class Ar, class Tin, class Tred, int R, int W, bool kVec16, bool kRef = false>
 __global__ void __launch_bounds__(W * 32)
     k_stage3(Level lv, const Tin* __restrict__ a, const Tin* __restrict__ b,
              const Tin* __restrict__ c, const Tin* __restrict__ d, const Tred* __restrict__ xred,
              const Tred* __restrict__ ck_gam, const Tred* __restrict__ ck_y,
-             const Tred* __restrict__ ck_v, Tin* __restrict__ x, int* __restrict__ status) {
+             const Tred* __restrict__ ck_v, Tin* __restrict__ x, int* __restrict__ status,
+             RefineIO rf = {}) {
   using T = typename Ar::T;
-  using TL = Tile<Tin, R>;
-  using TL3 = Tile3<Tin, Tred, R>;
+  using TL = Tile<Tin, R, kRef ? 5 : 4>;
+  using TL3 = Tile3<Tin, Tred, R, kRef ? 5 : 4>;
+  static_assert(!kRef || std::is_same<Tin, double>::value, "refinement steps are fp64");
   constexpr int V = TL::kVec;
   static_assert(sizeof(T) <= sizeof(Tin), "boundary chunks park T values in Tin slots");
   static_assert(sizeof(Tred) == 4 || sizeof(Tred) == 8, "checkpoint element size");
@@ -575,6 +695,7 @@ __global__ void __launch_bounds__(W * 32)
   Tin* tile = reinterpret_cast<Tin*>(wbase);
   Tred* ckbuf = reinterpret_cast<Tred*>(wbase + TL::kBytesPerWarp);  // [buf][3][32]
   const Tin* const srcs[4] = {a, b, c, d};
+  const Tin* const xsrc[1] = {x};  // refinement: the current iterate, a fifth array
   PieceMap<Tin, R> pm;
   pm.init(lv, k0, nb, lane);
   // the lane's checkpoint for chunk ch (written by Stage 1 after row ch*R-1)
@@ -587,8 +708,10 @@ __global__ void __launch_bounds__(W * 32)
     }
   };
   load_chunk<Tin, R, kVec16>(tile, srcs, 4, pm, (nch - 1) * R);
+  if constexpr (kRef) load_chunk<Tin, R, kVec16>(tile + 4 * TL::kArr, xsrc, 1, pm, (nch - 1) * R);
   load_ck(ckbuf, nch - 1);
   cp_async_commit();
+  unsigned long long mdel = 0, mx = 0;  // refinement maxima (bit patterns)
 
   const int64_t start = k * (int64_t)lv.m;
   Bounds bd;
@@ -608,6 +731,9 @@ __global__ void __launch_bounds__(W * 32)
     const int row0 = ch * R;
     if (ch > 0) {
       load_chunk<Tin, R, kVec16>(tile + ((it + 1) & 1) * TL::kBuf, srcs, 4, pm, row0 - R);
+      if constexpr (kRef)
+        load_chunk<Tin, R, kVec16>(tile + ((it + 1) & 1) * TL::kBuf + 4 * TL::kArr, xsrc, 1, pm,
+                                   row0 - R);
       load_ck(ckbuf + ((it + 1) & 1) * 96, ch - 1);
     }
     cp_async_commit();
@@ -667,6 +793,14 @@ __global__ void __launch_bounds__(W * 32)
       for (int r = 0; r < R; ++r) {
         Ar::to(xo[r], Z[r]);
         oob |= Ar::out_bad(xo[r]);
+        if constexpr (kRef) {  // x += delta (lanes past the level's last block: no rows)
+          const Tin xn = t[4 * TL::kArr + r] + xo[r];
+          if (active) {
+            mdel = max(mdel, abs_bits(xo[r]));
+            mx = max(mx, abs_bits(xn));
+          }
+          xo[r] = xn;
+        }
       }
 #pragma unroll
       for (int r = 0; r < R; r += V) {
@@ -715,6 +849,12 @@ __global__ void __launch_bounds__(W * 32)
           }
           Ar::to(t[r], xr);
           oob |= Ar::out_bad(t[r]);
+          if constexpr (kRef) {  // x += delta
+            const Tin xn = t[4 * TL::kArr + r] + t[r];
+            mdel = max(mdel, abs_bits(t[r]));
+            mx = max(mx, abs_bits(xn));
+            t[r] = xn;
+          }
         }
       }
     }
@@ -725,6 +865,17 @@ __global__ void __launch_bounds__(W * 32)
   }
   if (active && bad) atomicOr(status, ST_BAD_PIVOT);
   if (active && oob) atomicOr(status, ST_RANGE);
+  if constexpr (kRef) {
+    for (int o = 16; o > 0; o >>= 1) {
+      mdel = max(mdel, __shfl_xor_sync(0xffffffffu, mdel, o));
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    // most warps see maxima already raised past theirs: read before the atomic
+    if (lane == 0) {
+      if (mdel > *(volatile unsigned long long*)&rf.max2[0]) atomicMax(&rf.max2[0], mdel);
+      if (mx > *(volatile unsigned long long*)&rf.max2[1]) atomicMax(&rf.max2[1], mx);
+    }
+  }
 }
 
 // ------------------------------------------------------------------ small systems

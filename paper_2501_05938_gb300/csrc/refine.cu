@@ -10,6 +10,15 @@
 // stopping test reads two fp64 maxima back to the host after every
 // correction, so a mixed-precision solve synchronises its stream once per
 // iteration.
+//
+// Where the system is solved level by level (every size but those the
+// single-launch on-chip solve takes), a correction is one pass of the
+// partition method over the rows (refine_step): Stage 1 forms the residual
+// from the rows and x as it streams them and writes it out, Stage 3 reads
+// the residual back as its right-hand side and adds its result to x.  Per
+// row that moves a, b, c, d, x in and r out, then a, b, c, r, x in and x
+// out: 96 bytes against 144 for a residual pass, a solve and an update pass.
+// The on-chip route keeps the three separate passes below.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -87,6 +96,7 @@ tps_status run_refine(tps_plan_s* P, int64_t n, const double* a, const double* b
   const double tol = P->desc.tol > 0.0 ? P->desc.tol : 1e-12;
   P->last_iters = 0;
   P->last_corr = 0.0;
+  P->last_refine_fused = 0;
   // the first solve carries the range codes of the system (an fp32 x0 of a
   // right-hand side below the pairs' range would be 0 and 'converge'); the
   // corrections' right-hand sides are small by construction and skip them
@@ -98,14 +108,21 @@ tps_status run_refine(tps_plan_s* P, int64_t n, const double* a, const double* b
   tps_status st = run_solve(P, n, a, b, c, d, x, s, lv, nullptr, bnd, nbnd);
   if (st != TPS_OK) return st;
   P->codes_off = true;
+  // the fused step where level 0 runs as separate Stage 1 / Stage 3 sweeps
+  const bool fused = !lv.empty() && P->last_onchip != 1 && !P->test_unfused_refine;
+  P->last_refine_fused = fused ? 1 : 0;
   for (int it = 1; it <= max_iters; ++it) {
-    k_residual<<<grid_for(n), 256, 0, s>>>(n, a, b, c, d, x, r, bnd, nbnd);
-    if (cudaGetLastError() != cudaSuccess) return TPS_ERR_CUDA;
-    st = run_solve(P, n, a, b, c, r, dl, s, lv, nullptr, bnd, nbnd);
-    if (st != TPS_OK) return st;
-    if (cudaMemsetAsync(maxima, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess)
-      return TPS_ERR_CUDA;
-    k_update<<<grid_for(n), 256, 0, s>>>(n, x, dl, maxima);
+    if (fused) {
+      if (refine_step(P, lv, a, b, c, d, x, r, maxima, s) != cudaSuccess) return TPS_ERR_CUDA;
+    } else {
+      k_residual<<<grid_for(n), 256, 0, s>>>(n, a, b, c, d, x, r, bnd, nbnd);
+      if (cudaGetLastError() != cudaSuccess) return TPS_ERR_CUDA;
+      st = run_solve(P, n, a, b, c, r, dl, s, lv, nullptr, bnd, nbnd);
+      if (st != TPS_OK) return st;
+      if (cudaMemsetAsync(maxima, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess)
+        return TPS_ERR_CUDA;
+      k_update<<<grid_for(n), 256, 0, s>>>(n, x, dl, maxima);
+    }
     unsigned long long h[2];
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(h, maxima, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -226,40 +226,46 @@ static cudaError_t set_smem(K kernel, size_t smem, std::atomic<uint64_t>& done) 
 // Stage 1 streams chunks of K rows (or a multiple) and writes a checkpoint
 // every K rows, K being Stage 3's chunk length.
 #ifndef TPS_STAGE1_MUL
-#define TPS_STAGE1_MUL 1  // Stage-1 chunk rows = K * TPS_STAGE1_MUL (measured best: 1)
+#define TPS_STAGE1_MUL 1  // Stage-1 chunk rows = K * TPS_STAGE1_MUL / TPS_STAGE1_DIV
 #endif
-template <class Ar, class Tin, class Tred, int K>
+#ifndef TPS_STAGE1_DIV
+#define TPS_STAGE1_DIV 1
+#endif
+// kRef: a fused refinement step (RefineIO rf; fp64 arrays).
+template <class Ar, class Tin, class Tred, int K, bool kRef = false>
 static cudaError_t launch_stage1(const Level& lv, const Tin* a, const Tin* b, const Tin* c,
                                  const Tin* d, Tred* ra, Tred* rb, Tred* rc, Tred* rd, Tred* cg,
-                                 Tred* cy, Tred* cv, int* status, cudaStream_t s) {
+                                 Tred* cy, Tred* cv, int* status, cudaStream_t s,
+                                 RefineIO rf = {}) {
   constexpr int W = kWarpsPerCta;
-  constexpr int R = K * TPS_STAGE1_MUL;
-  const size_t smem = Tile<Tin, R>::kBytesPerWarp * W;
+  constexpr int R = K * TPS_STAGE1_MUL / TPS_STAGE1_DIV;
+  const size_t smem = Tile<Tin, R, kRef ? 5 : 4>::kBytesPerWarp * W;
   const int64_t warps = (lv.k_end - lv.k_begin + 31) / 32;
   const unsigned grid = (unsigned)((warps + W - 1) / W);
   if (grid == 0) return cudaSuccess;
-  const void* ptrs[4] = {a, b, c, d};
+  const void* ptrs[6] = {a, b, c, d, rf.x, rf.r};
   cudaError_t e;
-  if (vec16_ok<Tin>(lv.m, ptrs, 4)) {
+  if (vec16_ok<Tin>(lv.m, ptrs, kRef ? 6 : 4)) {
     static std::atomic<uint64_t> done{0};
-    auto k = k_stage1<Ar, Tin, Tred, R, K, W, true>;
+    auto k = k_stage1<Ar, Tin, Tred, R, K, W, true, kRef>;
     if ((e = set_smem(k, smem, done)) != cudaSuccess) return e;
-    k<<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, ra, rb, rc, rd, cg, cy, cv, status);
+    k<<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, ra, rb, rc, rd, cg, cy, cv, status, rf);
   } else {
     static std::atomic<uint64_t> done{0};
-    auto k = k_stage1<Ar, Tin, Tred, R, K, W, false>;
+    auto k = k_stage1<Ar, Tin, Tred, R, K, W, false, kRef>;
     if ((e = set_smem(k, smem, done)) != cudaSuccess) return e;
-    k<<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, ra, rb, rc, rd, cg, cy, cv, status);
+    k<<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, ra, rb, rc, rd, cg, cy, cv, status, rf);
   }
   return cudaGetLastError();
 }
 
-template <class Ar, class Tin, class Tred, int R>
+template <class Ar, class Tin, class Tred, int R, bool kRef = false>
 static cudaError_t launch_stage3(const Level& lv, const Tin* a, const Tin* b, const Tin* c,
                                  const Tin* d, const Tred* xr, const Tred* cg, const Tred* cy,
-                                 const Tred* cv, Tin* x, int* status, cudaStream_t s) {
+                                 const Tred* cv, Tin* x, int* status, cudaStream_t s,
+                                 RefineIO rf = {}) {
   constexpr int W = kWarpsPerCta;
-  const size_t smem = Tile3<Tin, Tred, R>::kBytesPerWarp * W;
+  const size_t smem = Tile3<Tin, Tred, R, kRef ? 5 : 4>::kBytesPerWarp * W;
   const int64_t warps = (lv.k_end - lv.k_begin + 31) / 32;
   const unsigned grid = (unsigned)((warps + W - 1) / W);
   if (grid == 0) return cudaSuccess;
@@ -267,14 +273,14 @@ static cudaError_t launch_stage3(const Level& lv, const Tin* a, const Tin* b, co
   cudaError_t e;
   if (vec16_ok<Tin>(lv.m, ptrs, 5)) {
     static std::atomic<uint64_t> done{0};
-    auto k = k_stage3<Ar, Tin, Tred, R, W, true>;
+    auto k = k_stage3<Ar, Tin, Tred, R, W, true, kRef>;
     if ((e = set_smem(k, smem, done)) != cudaSuccess) return e;
-    k<<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, xr, cg, cy, cv, x, status);
+    k<<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, xr, cg, cy, cv, x, status, rf);
   } else {
     static std::atomic<uint64_t> done{0};
-    auto k = k_stage3<Ar, Tin, Tred, R, W, false>;
+    auto k = k_stage3<Ar, Tin, Tred, R, W, false, kRef>;
     if ((e = set_smem(k, smem, done)) != cudaSuccess) return e;
-    k<<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, xr, cg, cy, cv, x, status);
+    k<<<grid, 32 * W, smem, s>>>(lv, a, b, c, d, xr, cg, cy, cv, x, status, rf);
   }
   return cudaGetLastError();
 }
@@ -407,6 +413,37 @@ cudaError_t stage3_range(tps_plan_s* P, const LevelPlan& L, int64_t kb, int64_t 
                                            (const Tin*)d, xr, ck[0], ck[1], ck[2], (Tin*)x,
                                            P->d_status, s);
   });
+}
+
+// One fused refinement step of the mixed solve on level 0 (fp64 arrays,
+// fp32 elimination): Stage 1 on the residual of x (written to r), the
+// reduced solve, Stage 3 adding the correction to x and raising max2.
+cudaError_t refine_step(tps_plan_s* P, const std::vector<LevelPlan>& levels, const double* a,
+                        const double* b, const double* c, const double* d, double* x, double* r,
+                        unsigned long long* max2, cudaStream_t s) {
+  using Ar = ArF32;
+  using Tin = double;
+  using Tred = float;
+  constexpr int R = kChunkRows<Tin>;
+  const LevelPlan& L = levels[0];
+  const RefineIO rf{x, r, max2};
+  Tred* red[5];
+  for (int i = 0; i < 5; ++i) red[i] = reinterpret_cast<Tred*>(P->ws + L.off_red[i]);
+  Tred* ck[3];
+  for (int i = 0; i < 3; ++i) ck[i] = reinterpret_cast<Tred*>(P->ws + L.off_ck[i]);
+  Level lv = L.lv;
+  lv.k_begin = 0;
+  lv.k_end = lv.p;
+  lv.dmax = nullptr;  // a residual's range codes are not judged
+  cudaError_t e = cudaMemsetAsync(max2, 0, 2 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess)
+    e = launch_stage1<Ar, Tin, Tred, R, true>(lv, a, b, c, d, red[0], red[1], red[2], red[3],
+                                              ck[0], ck[1], ck[2], P->d_status, s, rf);
+  if (e == cudaSuccess) e = reduced_solve(P, levels, s);
+  if (e == cudaSuccess)
+    e = launch_stage3<Ar, Tin, Tred, R, true>(lv, a, b, c, r, red[4], ck[0], ck[1], ck[2], x,
+                                              P->d_status, s, rf);
+  return e;
 }
 
 // Stage 2: the recursive solve of level 0's reduced system.

@@ -225,6 +225,10 @@ tps_status tps_plan(const tps_plan_desc* desc, tps_plan_t* out) {
 
   if (const char* t = std::getenv("TPS_TEST_ONCHIP_TIMEOUT"))
     P->test_barrier_extra = t[0] == '1';
+  // test switch: the mixed solve's corrections as three separate passes
+  // on every route (to compare them with the fused step)
+  if (const char* t = std::getenv("TPS_TEST_UNFUSED_REFINE"))
+    P->test_unfused_refine = t[0] == '1';
   if (d.flags & TPS_ZERO_COPY) {
     int dev = 0, v = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
@@ -769,6 +773,7 @@ tps_status tps_plan_query(tps_plan_t P, tps_info* out) {
   out->workspace_bytes = P->ws_needed;
   out->pageable_ok = (P->desc.flags & TPS_ZERO_COPY) && P->pageable_ok ? 1 : 0;
   out->onchip = P->last_onchip;
+  out->refine_fused = P->last_refine_fused;
   for (int i = 0; i < 4; ++i) out->stage_ms[i] = P->stage_ms[i];
   if (!P->ws) return TPS_OK;
   cudaStream_t s = P->last_stream;

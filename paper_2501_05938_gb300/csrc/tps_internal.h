@@ -113,6 +113,8 @@ struct tps_plan_s {
   // solve's grid barrier waits for one CTA more than it launches, so the
   // bounded wait runs out and the solve reports TPS_ERR_TIMEOUT
   bool test_barrier_extra = false;
+  bool test_unfused_refine = false;  // TPS_TEST_UNFUSED_REFINE=1 at plan time
+  int32_t last_refine_fused = 0;     // the last mixed solve used refine_step
   // batched work list (device) and its capacity in entries
   void* d_work = nullptr;
   size_t work_cap = 0;
@@ -147,6 +149,14 @@ cudaError_t stage3_range(tps_plan_s* P, const LevelPlan& L, int64_t kb, int64_t 
                          const void* a, const void* b, const void* c, const void* d, void* x,
                          cudaStream_t s);
 cudaError_t reduced_solve(tps_plan_s* P, const std::vector<LevelPlan>& levels, cudaStream_t s);
+// One correction step of the mixed solve fused into level 0's sweeps
+// (levels non-empty): r = d - A x (fp64) formed in Stage 1, the fp32 solve
+// of A delta = r, x += delta in Stage 3; max2 (two device words, zeroed
+// here) receives max |delta| and max |x| as non-negative double bit
+// patterns.  r: n doubles of scratch.
+cudaError_t refine_step(tps_plan_s* P, const std::vector<LevelPlan>& levels, const double* a,
+                        const double* b, const double* c, const double* d, double* x, double* r,
+                        unsigned long long* max2, cudaStream_t s);
 // Bytes of the on-chip solve's exchange rows (part of every plan workspace).
 size_t onchip_exchange_bytes();
 // The single-launch on-chip solve of one system if it fits on this device

@@ -538,13 +538,21 @@ def solve_cmd(args):
     ap.add_argument("--truncate", action="store_true")
     ap.add_argument("--no-onchip", action="store_true")
     ap.add_argument("--repeat", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=0)
+    ap.add_argument("--trace", action="store_true",
+                    help="per-stage event times (mean over the timed solves)")
     a = ap.parse_args(args)
     g = synth.system_device(1002, a.n)
     tdt = torch.float32 if a.dtype == "f32" else torch.float64
     arrs = [g[k].to(tdt) for k in "abcd"]
     x = torch.empty_like(arrs[1])
     flags = (binding.TRUNCATE if a.truncate else 0) | (binding.NO_ONCHIP if a.no_onchip else 0)
+    flags |= binding.TRACE if a.trace else 0
     plan = binding.Plan(a.n, dtype=a.dtype, m=a.m, m_reduced=a.m_reduced, flags=flags)
+    for _ in range(a.warmup):
+        plan.solve(*arrs, x)
+    if a.warmup:
+        plan.query()  # the trace averages over the timed solves only
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(a.repeat):
@@ -554,7 +562,8 @@ def solve_cmd(args):
     info = plan.query()
     print(json.dumps({"n": a.n, "dtype": a.dtype, "ms_per_solve": e0.elapsed_time(e1) / a.repeat,
                       "status": info["status_name"], "m": info["m"],
-                      "m_reduced": info["m_reduced"], "bound": info["last_correction"]}))
+                      "m_reduced": info["m_reduced"], "bound": info["last_correction"],
+                      **({"stage_ms": info["stage_ms"]} if a.trace else {})}))
     return 0 if info["status"] == 0 else 1
 
 
