@@ -307,10 +307,9 @@ tps_status tps_solve_host_many_async(tps_plan_t plan, int64_t count, int64_t n,
  * A system that fits in shared memory (every accepted size on a 152-SM
  * GB300) is solved by the single-launch on-chip solve (see tps_solve);
  * otherwise fixed parameters m = 64 at the top level, 32 below.  The first
- * call on a
- * device looks up the scratch array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream
- * capture.  Every call overwrites the shared scratch, so calls whose work
+ * call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current.  Every call overwrites
+ * the shared scratch, so calls whose work
  * overlaps on the GPU (other streams, other host threads) race and must be
  * serialised by the caller. */
 tps_status tps_solve_noalloc(int32_t dtype, int64_t n, const void* a, const void* b,
