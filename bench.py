@@ -15,7 +15,10 @@ Stage 2, Stage 3).
            inside the timed region, consecutive systems overlapped on two
            buffer sets so one system's D2H runs during the next one's H2D
            (median of three rounds of steps); h2d_floor_ms is the step's H2D
-           bytes as plain copies, the bound of that overlap.
+           bytes as plain copies, the bound of that overlap where the link
+           carries both directions at full rate; bidir_floor_ms the H2D and
+           the D2H as plain copies running at the same time, the bound where
+           the two directions share the link.
            e2e.single_call: one system per tps_solve_host_async call, whose
            bound is link_floor_ms (H2D, then D2H: no x leaves before every
            input arrived); e2e.zero_copy: single calls through
@@ -281,16 +284,19 @@ def time_host(plan, hk, hx, stream, steps, warmup, world):
 
 
 def link_floor(hk, hx, g, x, stream, reps=3):
-    """The host link's floors for one end-to-end step, as plain copies on one
-    stream: (H2D of a, b, c, d then D2H of x, H2D alone).  Within one system
-    no part of x can leave before every input has arrived (the reduced system
+    """The host link's floors for one end-to-end step, as plain copies:
+    (H2D of a, b, c, d then D2H of x on one stream, H2D alone, H2D with the
+    D2H running at the same time on a second stream).  Within one system no
+    part of x can leave before every input has arrived (the reduced system
     couples all rows), so the first is the floor of a single solve; when
     consecutive systems overlap, one system's D2H runs during the next one's
-    H2D and the H2D alone is the floor.  Copying g's own values back into g
-    leaves the system unchanged."""
+    H2D: the H2D alone is the floor if the link carries both directions at
+    full rate, the concurrent pair if they share it.  Copying g's own values
+    back into g leaves the system unchanged."""
     import torch
 
-    best, best_h2d = float("inf"), float("inf")
+    best, best_h2d, best_bi = float("inf"), float("inf"), float("inf")
+    s2 = torch.cuda.Stream()
     for _ in range(reps):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         ev[0].record(stream)
@@ -303,7 +309,21 @@ def link_floor(hk, hx, g, x, stream, reps=3):
         stream.synchronize()
         best = min(best, ev[0].elapsed_time(ev[2]))
         best_h2d = min(best_h2d, ev[0].elapsed_time(ev[1]))
-    return best, best_h2d
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s2.wait_event(e0)
+        with torch.cuda.stream(stream):
+            for k in "abcd":
+                g[k].copy_(hk[k], non_blocking=True)
+        with torch.cuda.stream(s2):
+            hx.copy_(x, non_blocking=True)
+        done2 = torch.cuda.Event()
+        done2.record(s2)
+        stream.wait_event(done2)
+        e1.record(stream)
+        stream.synchronize()
+        best_bi = min(best_bi, e0.elapsed_time(e1))
+    return best, best_h2d, best_bi
 
 
 def verify(g, x):
@@ -693,7 +713,7 @@ def main():
         single_ms = statistics.median(singles)
         single_ms_pred = statistics.median(singles_pred)
         del plan_hp
-        floor_ms, h2d_ms = link_floor(hk, hx, g, x, stream)
+        floor_ms, h2d_ms, bidir_ms = link_floor(hk, hx, g, x, stream)
         del plan_h
         # zero copy: kernels on host memory, pinned and pageable
         zc = {}
@@ -789,6 +809,7 @@ def main():
                 "call": "tps_solve_host_many_async: consecutive systems overlap, each "
                         "system's D2H runs during the next one's H2D",
                 "rounds_ms": rounds, "h2d_floor_ms": h2d_ms, "frac_of_h2d_floor": h2d_ms / ems,
+                "bidir_floor_ms": bidir_ms, "frac_of_bidir_floor": bidir_ms / ems,
                 "link_floor_ms": floor_ms,
                 "single_call": {"value": world * n / (single_ms * 1e-3), "ms_per_step": single_ms,
                                 "call": "tps_solve_host_async, one system per call",
