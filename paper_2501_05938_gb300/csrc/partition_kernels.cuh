@@ -361,8 +361,14 @@ __device__ __forceinline__ double residual_row(double a, double b, double c, dou
   r = fma(-a, xm, r);
   return fma(-c, xp, r);
 }
+// |v|'s bit pattern from integer operations on the two halves (masking the
+// sign of the 64-bit pattern is compiled as an fp64 absolute value, an
+// instruction of the slow fp64 pipe: measured 2 of the 3 fp64 instructions
+// per row of the refinement's Stage 3)
 __device__ __forceinline__ unsigned long long abs_bits(double v) {
-  return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned hi = (unsigned)__double2hiint(v) & 0x7FFFFFFFu;
+  const unsigned lo = (unsigned)__double2loint(v);
+  return ((unsigned long long)hi << 32) | lo;
 }
 
 // chunks the warp iterates: the longest block of the warp decides
