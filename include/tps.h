@@ -197,6 +197,14 @@ tps_status tps_set_workspace(tps_plan_t plan, void* dev_ptr, size_t bytes);
  * on-chip solves of different streams one after the other, or use
  * TPS_NO_ONCHIP for plans that run concurrently.
  *
+ * TPS_MIXED_F32_F64: x0 from an fp32 elimination of the fp64 inputs, then
+ * corrections until ||delta||/||x|| <= tol or max_iters.  Where the system
+ * is solved level by level, each correction is one fused pass of the
+ * partition method: Stage 1 forms r = d - A x in fp64 from the rows and the
+ * current x (writing r to the workspace), Stage 3 adds the fp32 solution of
+ * A delta = r to x in place (tps_info.refine_fused = 1); the single-launch
+ * on-chip route keeps a separate residual pass, solve and update pass.
+ *
  * TPS_TRUNCATE (device plans, fp64 / double-float / fp32; not the paper's
  * method, an approximation for strongly dominant systems): windows of m kept
  * rows are solved independently, each as the system on the window plus
@@ -206,7 +214,8 @@ tps_status tps_set_workspace(tps_plan_t plan, void* dev_ptr, size_t bytes);
  * window, on chip) or m + 2 m_reduced = 32 mb with 8 <= mb <= 256 (one warp
  * per window: 32 blocks of mb rows, one per lane, the partition method
  * inside the warp, the blocks' row relations kept in a workspace buffer of
- * about 24 bytes per row that stays mostly in L2); 0 chooses (the halo for
+ * about 24 bytes per row, written once and read back once; at the default
+ * window size about two thirds of it round-trip through DRAM); 0 chooses (the halo for
  * the plan's tol at a dominance factor max(|a|+|c|)/|b| of 3/4, one-warp
  * windows of 32 blocks of 256 rows).  Each window bounds its own error from
  * its dominance factor q and smallest |b|: (|a_cut| q^h + |c_cut| q^h) /

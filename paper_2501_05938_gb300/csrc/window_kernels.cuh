@@ -14,9 +14,10 @@
 //            per-row quantities are the interior row's relation
 //                x_j = g'_j - alpha'_j f - c'_j x_{j+1},
 //            (c'_j, g'_j, alpha'_j) = (c_j, g_j, alpha_j) / beta_j, written to
-//            the window's slice of a relation buffer (L2-resident: the warp
-//            reads it back soon and then discards it, so it never has to be
-//            written back to DRAM), and forms the block's two reduced rows;
+//            the window's slice of a relation buffer (read back once and then
+//            discarded from L2; what L2 still holds at that point never goes
+//            to DRAM, at the default window size about a third), and forms
+//            the block's two reduced rows;
 //   Stage 2  the window's 64 reduced rows, with the couplings that leave the
 //            extended range cut, by parallel cyclic reduction in the warp;
 //   Stage 3  every lane walks its block bottom-up through the relations
