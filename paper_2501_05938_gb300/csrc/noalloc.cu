@@ -123,10 +123,10 @@ cudaError_t run(unsigned char* ws, const Layout& L, int idx, int64_t n, const Ti
   const void* in4[4] = {a, b, c, d};
   const void* in5[5] = {a, b, c, d, x};
   if (aligned16<Tin>(P.lv.m, in4, 4))
-    k_stage1<Ar, Tin, Tred, R1, K, 1, true><<<grid, 32, Tile<Tin, R1>::kBytesPerWarp, s>>>(
+    k_stage1<Ar, Tin, Tred, R1, K, 1, true><<<grid, 32, stage1_smem_per_warp<Tin, R1>(), s>>>(
         lv, a, b, c, d, red[0], red[1], red[2], red[3], ck[0], ck[1], ck[2], st);
   else
-    k_stage1<Ar, Tin, Tred, R1, K, 1, false><<<grid, 32, Tile<Tin, R1>::kBytesPerWarp, s>>>(
+    k_stage1<Ar, Tin, Tred, R1, K, 1, false><<<grid, 32, stage1_smem_per_warp<Tin, R1>(), s>>>(
         lv, a, b, c, d, red[0], red[1], red[2], red[3], ck[0], ck[1], ck[2], st);
   if (dmax) k_dcode_check<<<1, 256, 0, s>>>(dmax, 1, st);
   cudaError_t e = cudaGetLastError();

@@ -401,6 +401,19 @@ __device__ __forceinline__ int chunk_kind(int ch, int row0, int R, int lmin, int
 }
 
 // ------------------------------------------------------------------ Stage 1
+// Chunk buffers per warp in Stage 1's copy pipeline (2: the next chunk is
+// copied while one is processed).
+#ifndef TPS_STAGE1_STAGES
+#define TPS_STAGE1_STAGES 2
+#endif
+constexpr int kS1Stages = TPS_STAGE1_STAGES;
+static_assert(kS1Stages >= 2 && kS1Stages <= 4, "Stage-1 pipeline depth");
+// Shared memory of one Stage-1 warp (NA arrays per buffer).
+template <class Tin, int R, int NA = 4>
+constexpr size_t stage1_smem_per_warp() {
+  return Tile<Tin, R, NA>::kBytesPerWarp / 2 * kS1Stages;
+}
+
 // R rows per chunk; a checkpoint every K rows (K the chunk length of
 // Stage 3; one of R and K divides the other).  kRef: a refinement step
 // (RefineIO), the right-hand side being the residual of rf.x.
@@ -428,17 +441,24 @@ __global__ void __launch_bounds__(W * 32)
   const int lmin = warp_lmin(lv, k0, nb);
   const int luni = warp_luni(lv, k0, nb);
 
-  Tin* tile = reinterpret_cast<Tin*>(smem_raw) + warp * 2 * TL::kBuf;
+  Tin* tile = reinterpret_cast<Tin*>(smem_raw) + warp * kS1Stages * TL::kBuf;
   const Tin* const srcs[4] = {a, b, c, d};
   PieceMap<Tin, R> pm;
   pm.init(lv, k0, nb, lane);
-  load_chunk<Tin, R, kVec16>(tile, srcs, 4, pm, 0);
   XPieceMap<Tin, R> xpm;
-  if constexpr (kRef) {
-    xpm.init(lv, k0, nb, lane);
-    load_xchunk<Tin, R, kVec16>(tile + 4 * TL::kArr, (const Tin*)rf.x, xpm, 0, lv.n);
-  }
-  cp_async_commit();
+  if constexpr (kRef) xpm.init(lv, k0, nb, lane);
+  // chunk c goes to buffer c % kS1Stages, one commit group per chunk
+  auto fetch = [&](int c) {
+    if (c < nch) {
+      Tin* buf = tile + (c % kS1Stages) * TL::kBuf;
+      load_chunk<Tin, R, kVec16>(buf, srcs, 4, pm, c * R);
+      if constexpr (kRef)
+        load_xchunk<Tin, R, kVec16>(buf + 4 * TL::kArr, (const Tin*)rf.x, xpm, c * R, lv.n);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int c = 0; c < kS1Stages - 1; ++c) fetch(c);
   const int64_t start = k * (int64_t)lv.m;
   Bounds bd;
   bd.init(lv, start, L, active);
@@ -511,16 +531,10 @@ __global__ void __launch_bounds__(W * 32)
 
   for (int ch = 0; ch < nch; ++ch) {
     const int row0 = ch * R;
-    if (ch + 1 < nch) {
-      Tin* nxt = tile + ((ch + 1) & 1) * TL::kBuf;
-      load_chunk<Tin, R, kVec16>(nxt, srcs, 4, pm, row0 + R);
-      if constexpr (kRef)
-        load_xchunk<Tin, R, kVec16>(nxt + 4 * TL::kArr, (const Tin*)rf.x, xpm, row0 + R, lv.n);
-    }
-    cp_async_commit();
-    cp_async_wait<1>();
+    fetch(ch + kS1Stages - 1);
+    cp_async_wait<kS1Stages - 1>();
     __syncwarp();
-    Tin* const tb = tile + (ch & 1) * TL::kBuf;
+    Tin* const tb = tile + (ch % kS1Stages) * TL::kBuf;
     Tin* const t = tb + lane * TL::kStride;
     const bool clean = !__any_sync(0xffffffffu, bd.cnt > 0 && bd.touches(start + row0, R));
     const int kind = chunk_kind(ch, row0, R, lmin, luni, clean);

@@ -239,7 +239,7 @@ static cudaError_t launch_stage1(const Level& lv, const Tin* a, const Tin* b, co
                                  RefineIO rf = {}) {
   constexpr int W = kWarpsPerCta;
   constexpr int R = K * TPS_STAGE1_MUL / TPS_STAGE1_DIV;
-  const size_t smem = Tile<Tin, R, kRef ? 5 : 4>::kBytesPerWarp * W;
+  const size_t smem = stage1_smem_per_warp<Tin, R, kRef ? 5 : 4>() * W;
   const int64_t warps = (lv.k_end - lv.k_begin + 31) / 32;
   const unsigned grid = (unsigned)((warps + W - 1) / W);
   if (grid == 0) return cudaSuccess;
