@@ -29,6 +29,7 @@
 #include <stdint.h>
 
 #include "partition_kernels.cuh"
+#include "window_bound.cuh"
 
 namespace tps {
 
@@ -466,9 +467,6 @@ struct WinLayout {
   __host__ __device__ static constexpr size_t bytes(int rows) { return 4 * (kLv + l0(rows)); }
 };
 
-__device__ __forceinline__ float abs_f(double v) { return (float)fabs(v); }
-__device__ __forceinline__ float abs_f(float v) { return fabsf(v); }
-__device__ __forceinline__ float abs_f(float2 v) { return fabsf(v.x); }
 
 // R, h even; one CTA per window.
 template <class Ar, class Tin>
@@ -488,8 +486,8 @@ __global__ void __launch_bounds__(kWinThreads)
     lv[k] = reinterpret_cast<T*>(smem_raw + k * Lay::kLv);
     s0[k] = reinterpret_cast<Tin*>(smem_raw + 4 * Lay::kLv + k * l0);
   }
-  __shared__ unsigned q_bits, bmin_bits;
-  __shared__ float cut_s[2];
+  __shared__ unsigned q_bits, bmin_key;
+  __shared__ Tin cut_s[2];
   const int tid = (int)threadIdx.x;
   const int64_t k0 = (int64_t)blockIdx.x * R;
   const int64_t k1 = k0 + R < n ? k0 + R : n;
@@ -511,27 +509,26 @@ __global__ void __launch_bounds__(kWinThreads)
   cp_async_wait<0>();
   __syncthreads();  // every thread's copies have landed
   if (tid == 0) {
-    cut_s[0] = e0 > 0 ? abs_f(s0[0][0]) : 0.0f;  // the couplings being cut
-    cut_s[1] = e1 < n ? abs_f(s0[2][E - 1]) : 0.0f;
+    cut_s[0] = e0 > 0 ? s0[0][0] : Tin{};  // the couplings being cut
+    cut_s[1] = e1 < n ? s0[2][E - 1] : Tin{};
     q_bits = 0u;
-    bmin_bits = 0x7f800000u;  // +inf
+    bmin_key = 0x7FFFFFFFu;
     s0[0][0] = Tin{};
     s0[2][E - 1] = Tin{};
   }
   __syncthreads();
-  // ---- q and min |b| of the window (cut couplings zero), rounded up / down
-  float qmax = 0.0f, bmin = __int_as_float(0x7f800000);
+  // ---- q and min |b| of the window (cut couplings zero): q per row from
+  // the scaled row, rounded up; min |b| as the smallest magnitude key
+  float qmax = 0.0f;
+  unsigned bkey = 0x7FFFFFFFu;
   for (int i = tid; i < E; i += kWinThreads) {
-    const float bb = abs_f(s0[1][i]);
-    const float qq = __fdiv_ru(__fadd_ru(abs_f(s0[0][i]), abs_f(s0[2][i])), bb);
-    qmax = fmaxf(qmax, qq);
-    bmin = fminf(bmin, bb);
+    qmax = fmaxf(qmax, win_row_q(s0[0][i], s0[1][i], s0[2][i]));
+    bkey = min(bkey, mag_key(s0[1][i]));
   }
-  // |b| from hi parts and fp32 rounding: widen q by a relative 2^-20 margin
+  // truncated parts and fp32 rounding: widen q by a relative 2^-20 margin
   qmax = __fmul_ru(qmax, 1.0f + 9.5367431640625e-07f);
-  bmin = __fmul_rd(bmin, 1.0f - 9.5367431640625e-07f);
   atomicMax(&q_bits, __float_as_uint(qmax));
-  atomicMin(&bmin_bits, __float_as_uint(bmin));
+  atomicMin(&bmin_key, bkey);
   __syncthreads();  // every row read before Stage 1 overwrites a, b, c in place
 
   // ---- Stage 1: thread blocks of mt rows (odd) over the E rows, then levels
@@ -597,15 +594,29 @@ __global__ void __launch_bounds__(kWinThreads)
 
   // ---- the window's truncation bound
   if (tid == 0) {
-    const float q = __uint_as_float(q_bits), bm = __uint_as_float(bmin_bits);
+    const float q = __uint_as_float(q_bits);
+    // |a_cut| / min |b| and |c_cut| / min |b|, rounded up (scale-free, so a
+    // system scaled anywhere in the input's range gets the same bound)
+    float ra, rc;
+    if constexpr (sizeof(Tin) == 8) {
+      const double bmd = __hiloint2double((int)bmin_key, 0);
+      ra = __double2float_ru(__ddiv_ru(fabs((double)cut_s[0]), bmd));
+      rc = __double2float_ru(__ddiv_ru(fabs((double)cut_s[1]), bmd));
+    } else {
+      const float bmf = __uint_as_float(bmin_key);
+      ra = __fdiv_ru(fabsf((float)cut_s[0]), bmf);
+      rc = __fdiv_ru(fabsf((float)cut_s[1]), bmf);
+    }
     float eps;
-    if (cut_s[0] == 0.0f && cut_s[1] == 0.0f) {
+    if (ra == 0.0f && rc == 0.0f) {
       eps = 0.0f;  // nothing cut
-    } else if (!(q < 1.0f) || !(bm > 0.0f)) {
+    } else if (!(q < 1.0f) || !(ra < __int_as_float(0x7f800000)) ||
+               !(rc < __int_as_float(0x7f800000))) {
       eps = __int_as_float(0x7f800000);
     } else {
-      const float num = cut_s[0] * powf(q, (float)o) + cut_s[1] * powf(q, (float)(e1 - k1));
-      eps = __fdiv_ru(num, __fmul_rd(1.0f - q, bm)) * (1.0f + 1e-5f);
+      const float num = __fadd_ru(__fmul_ru(ra, powf(q, (float)o)),
+                                  __fmul_ru(rc, powf(q, (float)(e1 - k1))));
+      eps = __fdiv_ru(num, __fsub_rd(1.0f, q)) * (1.0f + 1e-5f);
     }
     atomicMax(bound_max, __float_as_uint(eps));
     if (!(eps <= tol)) atomicOr(status, ST_NO_CONVERGENCE);

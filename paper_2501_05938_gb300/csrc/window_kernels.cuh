@@ -34,6 +34,7 @@
 #include <stdint.h>
 
 #include "partition_kernels.cuh"
+#include "window_bound.cuh"
 
 namespace tps {
 
@@ -129,7 +130,6 @@ __device__ __forceinline__ void store_kept(Tin* __restrict__ x, const Tin* buf,
 // high part of a pair, or the value rounded (native fp64: a conversion
 // instruction of the slow fp64 pipe; that path is bound by the pipe anyway).
 __device__ __forceinline__ float lead_f32(const df64& v) { return v.hi; }
-__device__ __forceinline__ float lead_f32(double v) { return (float)v; }
 __device__ __forceinline__ float lead_f32(float v) { return v; }
 
 __device__ __forceinline__ void discard_l2(const void* p) {
@@ -210,9 +210,14 @@ __global__ void __launch_bounds__(32)
   // dominance of one row (cut couplings 0): (|a| + |c|) / |b| from the
   // arithmetic's values, the reciprocal approximate (the bound widens q)
   auto dominance = [&](const T& av, const T& bv, const T& cv) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(fabsf(lead_f32(bv))));
-    qmax = fmaxf(qmax, (fabsf(lead_f32(av)) + fabsf(lead_f32(cv))) * r);
+    if constexpr (std::is_same<T, double>::value) {
+      // native fp64 rows are not scaled: their ratio from the scaled split
+      qmax = fmaxf(qmax, win_row_q(av, bv, cv));
+    } else {
+      float r;
+      asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(fabsf(lead_f32(bv))));
+      qmax = fmaxf(qmax, (fabsf(lead_f32(av)) + fabsf(lead_f32(cv))) * r);
+    }
   };
   auto bmin_raw = [&](Tin bin) {
     unsigned wv;

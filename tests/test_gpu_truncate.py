@@ -157,3 +157,23 @@ def test_full_size_against_the_exact_oracle():
     xs = x.cpu().numpy()
     assert oracle.rel_forward_error(xs, ref) <= 1e-10
     assert oracle.rel_residual(a, b, c, d, xs) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f64_df"])
+@pytest.mark.parametrize("R,h", [(1584, 104), (1840, 104)])  # one-CTA, one-warp windows
+@pytest.mark.parametrize("rows", [2.0 ** -600, 2.0 ** 300])
+def test_bound_is_scale_free(dtype, R, h, rows):
+    """Every row multiplied by the same power of two: x is unchanged, and so
+    is each window's bound (a ratio of couplings to diagonals), also far
+    outside binary32's range, where a bound computed from fp32 copies of the
+    entries would under- or overflow."""
+    n = 100003
+    s = synth.system(88, n)
+    t = {k: np.asarray(s[k], dtype=np.float64) * rows for k in "abcd"}
+    plan = binding.Plan(n, dtype=dtype, m=R, m_reduced=h, tol=1.0, flags=binding.TRUNCATE)
+    x0, i0 = run(plan, s)
+    x1, i1 = run(plan, t)
+    assert i0["status"] == 0 and i1["status"] == 0, (i0, i1)
+    assert oracle.rel_forward_error(x1, x0) <= 1e-14
+    assert 0.0 < i0["last_correction"] < 1e-12
+    assert abs(i1["last_correction"] - i0["last_correction"]) <= 1e-5 * i0["last_correction"]
