@@ -562,12 +562,17 @@ __global__ void __launch_bounds__(kWinThreads)
     const AccLv<Ar> A{{lv[0], lv[1], lv[2], lv[3]}, lev.off};
     RowChk nochk;
     oc_fwd<Ar>(A, lev.N, red, bad, nochk);
-    // b1 f + c1 l = d1;  a2 f + b2 l = d2
-    const T det = Ar::sub_mul(Ar::mul(red[1], red[5]), red[2], red[4]);
-    bad |= Ar::bad_pivot(det);
-    const T rdet = Ar::rcp(det);
-    const T f = Ar::mul(Ar::sub_mul(Ar::mul(red[3], red[5]), red[2], red[7]), rdet);
-    const T l = Ar::mul(Ar::sub_mul(Ar::mul(red[1], red[7]), red[4], red[3]), rdet);
+    // b1 f + c1 l = d1;  a2 f + b2 l = d2, eliminated as two Thomas rows:
+    // no product of two pivots is formed (native fp64 rows of any scale,
+    // e.g. 2^-600, whose determinant would underflow)
+    bad |= Ar::bad_pivot(red[1]);
+    const T r1 = Ar::rcp(red[1]);
+    const T g1 = Ar::mul(red[2], r1);  // c1 / b1
+    const T z1 = Ar::mul(red[3], r1);  // d1 / b1
+    const T b2p = Ar::sub_mul(red[5], red[4], g1);
+    bad |= Ar::bad_pivot(b2p);
+    const T l = Ar::mul(Ar::sub_mul(red[7], red[4], z1), Ar::rcp(b2p));
+    const T f = Ar::sub_mul(z1, g1, l);
     oc_bwd<Ar>(A, lev.N, f, l);
   }
   __syncthreads();
