@@ -10,7 +10,9 @@
  *   Stage 3  per block: recover the interior unknowns from the interface
  *            values.
  * Here all three stages run on the GPU; Stage 2 applies the same method
- * recursively and finishes with parallel cyclic reduction in one warp.  The
+ * recursively until the reduced system fits in shared memory (one
+ * cooperative launch finishes it) or in one warp (parallel cyclic
+ * reduction).  The
  * host-resident pipeline (Sec. 2.2, Eq. 2) overlaps chunked host-to-device
  * copies, kernels and device-to-host copies on S CUDA streams, S a power of
  * two up to 32 (Sec. 2.1).
