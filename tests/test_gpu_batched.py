@@ -12,7 +12,8 @@ from paper_2501_05938_gb300 import binding, synth
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": (1e-10, 1e-12), "f64_df": (1e-10, 1e-12), "f32": (1e-5, 1e-5)}
+TOL = {"f64": (1e-10, 1e-12), "f64_df": (1e-10, 1e-12), "f32": (1e-5, 1e-5),
+       "mixed": (1e-10, 1e-12)}
 
 
 def poisoned(s, off):
@@ -48,14 +49,18 @@ def run_batch(dtype, sizes, seed=5, m=0):
     return info, xs, ref, s64, off
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f64_df", "f32"])
+# mixed: the refinement's corrections run fused into level 0, so its residual
+# (formed in Stage 1) must not read the poisoned couplings either
+@pytest.mark.parametrize("dtype", ["f64", "f64_df", "f32", "mixed"])
 @pytest.mark.parametrize("sizes,m", [([1], 32), ([5, 0, 1, 2], 32), ([40, 24], 8),
                                      ([0, 300, 1, 1, 2, 65, 64, 63, 0, 1000], 32),
                                      ([1000, 17, 3000, 1, 4097], 64), ([7] * 300, 16),
                                      ([70000, 1, 129, 65537], 0)])
 def test_small_batches(dtype, sizes, m):
     info, xs, ref, s64, off = run_batch(dtype, sizes, m=m)
-    assert info["status"] == 0
+    assert info["status"] == 0, info
+    if dtype == "mixed" and sum(sizes) > 64:
+        assert info["refine_fused"]
     fwd, res = TOL[dtype]
     assert oracle.rel_forward_error(xs, ref) <= fwd
     r = oracle.residual_batched(off, s64["a"], s64["b"], s64["c"], s64["d"], xs)
